@@ -1,0 +1,306 @@
+"""Benchmark of the NMFA hot path on one GB300 (or N GPUs, one process each).
+
+Workload (one "step" = one full run of Algorithm 1 plus readout and energies):
+Sherrington-Kirkpatrick instance, N = 2000 spins, J_ij = +-1 symmetric, h = 0,
+1024 replicas, t_f = 1000 steps, sigma = alpha = 0.15, the default three-segment
+schedule; J and S in BF16 with FP32 accumulation on the tcgen05 tensor cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nmfa|reference]
+
+Prints one JSON line.  `value` is whole-job spin-updates/s with inputs resident in
+HBM; `e2e` is the same metric through the host-buffer C call (nmfa_run) with the
+temperature upload and the sign/energy download inside the timed region.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the workload.
+Multi-GPU: each rank runs its own replicas (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NMFA spin-updates/s and p50/p99 time-to-target vs plain FP32 path, one GB300"
+N_SPINS, REPLICAS, T_F = 2000, 1024, 1000
+SIGMA = ALPHA = 0.15
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, powers = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                powers.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(powers) if powers else None}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(sample_replicas=16, sample_steps=200, nthreads=0):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: the same
+    instance and schedule, `sample_replicas` replicas over the first `sample_steps`
+    steps, OpenMP over replicas on every host core."""
+    import numpy as np
+
+    import oracle
+    from paper_1806_08422_gb300 import instances as inst
+
+    J = inst.sk(N_SPINS, 0)
+    T = inst.schedule(T_F)[:sample_steps]
+    cores = os.cpu_count() if nthreads <= 0 else nthreads
+    t0 = time.perf_counter()
+    oracle.run(J, T, SIGMA, ALPHA, sample_replicas, seed=0, nthreads=cores)
+    dt = time.perf_counter() - t0
+    units = sample_replicas * N_SPINS * sample_steps
+    return {"value": units / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+            "sample": "SK N=%d, %d replicas x first %d of %d steps (FP64 C oracle, OpenMP over replicas), %.2f s"
+                      % (N_SPINS, sample_replicas, sample_steps, T_F, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_baseline(sample_replicas=16, sample_steps=20)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(sample_replicas=16, sample_steps=50))
+    wall = time.perf_counter() - t_all
+    units = sum(16 * N_SPINS * 50 for _ in vals)
+    value = units / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "SK N=2000 +-1, h=0, sigma=alpha=0.15, default schedule; each step a bounded "
+                                   "sample: 16 replicas x 50 steps of the 1024-replica, 1000-step run"},
+            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "16 replicas x 50 steps per bench step"},
+            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nmfa", choices=["nmfa", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1806_08422_gb300 import instances as inst
+    from paper_1806_08422_gb300 import nmfa
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(nmfa.LIB_PATH):
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    J = inst.sk(N_SPINS, 0)
+    T = inst.schedule(T_F)
+    prob = nmfa.Problem(J, precision=args.precision)
+    Td = torch.as_tensor(T, device=dev)
+    signs = torch.empty((REPLICAS, N_SPINS), dtype=torch.int8, device=dev)
+    energy = torch.empty(REPLICAS, dtype=torch.float64, device=dev)
+    energy_i64 = torch.empty(REPLICAS, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream_id = rank  # each rank anneals its own independent replicas
+
+    def one_step():
+        prob.run_device(Td, SIGMA, ALPHA, REPLICAS, seed=0, stream_id=stream_id, signs=signs, energy=energy,
+                        energy_i64=energy_i64, stream=stream)
+
+    nmfa.nmfa_profile_enable(prob.handle, True)
+    for _ in range(args.warmup):
+        one_step()
+    prob.sync()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = nmfa.nmfa_launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the step events)
+        ev[k][0].record(stream)
+        one_step()
+        ev[k][1].record(stream)
+        kernel_ms.append(None)
+        torch.cuda.synchronize()
+        kernel_ms[-1] = nmfa.nmfa_last_kernel_ms(prob.handle)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = nmfa.nmfa_launch_count() - launches0
+    clocks = sampler.stop()
+    prob.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = REPLICAS * N_SPINS * T_F
+    value = units_per_step * ws * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer C call (T upload, signs + energies download)
+    nmfa.nmfa_profile_enable(prob.handle, False)
+    e2e_steps = max(3, min(args.steps, 5))
+    nmfa.nmfa_run(prob.handle, N_SPINS, T, SIGMA, ALPHA, REPLICAS, 0, stream_id, True)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        nmfa.nmfa_run(prob.handle, N_SPINS, T, SIGMA, ALPHA, REPLICAS, 0, stream_id, True)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": units_per_step * ws / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": T_F * 8,
+           "d2h_bytes_per_step": REPLICAS * N_SPINS + REPLICAS * 8 * 2}
+
+    peaks, peak_kind = _peaks()
+    kern_ms = statistics.mean(kernel_ms)
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * T_F
+    if args.precision == "bf16":
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "nmfa_tc_kernel<128>", "kernel_ms": kern_ms,
+                    "peak_source": "%s bf16_tflops_sustained" % peak_kind}
+    else:
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel_ms": kern_ms}
+
+    extra = {}
+    if rank == 0 and not args.no_fp32_compare and args.precision != "fp32":
+        # the plain FP32 per-instance CUDA-core path on the same workload
+        p32 = nmfa.Problem(J, precision="fp32")
+        nmfa.nmfa_profile_enable(p32.handle, True)
+        p32.run_device(Td, SIGMA, ALPHA, REPLICAS, signs=signs, energy=energy, stream=stream)
+        p32.sync()
+        ms32 = []
+        for _ in range(2):
+            p32.run_device(Td, SIGMA, ALPHA, REPLICAS, signs=signs, energy=energy, stream=stream)
+            p32.sync()
+            ms32.append(nmfa.nmfa_last_kernel_ms(p32.handle))
+        extra["fp32_path"] = {"value": units_per_step / (statistics.mean(ms32) / 1e3), "unit": "spin-updates/s",
+                              "kernel_ms": statistics.mean(ms32)}
+        p32.close()
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline()
+        line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": "SK N=2000 J=+-1 h=0, 1024 replicas, t_f=1000, sigma=alpha=0.15, "
+                                       "default 3-segment schedule; %s" % (
+                                           "BF16 J/S, FP32 accumulation on tcgen05" if args.precision == "bf16"
+                                           else args.precision + " CUDA-core path"),
+                           "n": N_SPINS, "replicas_per_gpu": REPLICAS, "t_f": T_F,
+                           "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                           "parallelism": "replicas" if ws == 1 else "replicas x%d ranks" % ws},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "wall_s_timed": t_wall, "step_ms": step_ms}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * nmfa.h -- C ABI of libnmfa.so: noisy mean-field annealing (NMFA, Algorithm 1 of
+ * King, Bernoudy, King, Berkley, Lanting, "Emulating the coherent Ising machine with
+ * a mean-field algorithm", arXiv 1806.08422) on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Algorithm 1): for an Ising problem (h, J) on n spins, start every
+ * spin at s_i = 0; for t = 1..t_f compute, from the old state, for every i
+ *     Phi_i = (h_i + sum_j J_ij s_j) / sqrt(h_i^2 + sum_j J_ij^2) + N(0, sigma)
+ *     sh_i  = -tanh(Phi_i / T_t)
+ * and only then set s_i := alpha sh_i + (1 - alpha) s_i for every i; finally read
+ * out the signs ~s_i = s_i / |s_i|.  The energy of a sign vector is Eq. (1),
+ *     H = sum_{i<j} J_ij ~s_i ~s_j + sum_i h_i ~s_i,
+ * each unordered pair counted once.
+ *
+ * Conventions shared by every entry point:
+ *  - All calls return an int status: NMFA_OK (0) or a negative NMFA_E* code; the
+ *    thread-local message of the last failure is nmfa_last_error().  On failure no
+ *    output buffer is written (except where noted) and a handle stays usable.
+ *  - J is symmetric with a zero diagonal (otherwise NMFA_ENOTSYM / NMFA_EDIAG);
+ *    h may be NULL, meaning h = 0.  Dense J is row-major n*n float64.
+ *  - A run draws R = `replicas` independent replicas r = 0..R-1.  Its Gaussian draw
+ *    for (replica r, step t, spin i) is Box-Muller on Philox4x32-10 with counter
+ *    (r/4, t, i, stream_id) and key (seed & 0xffffffff, seed >> 32), steps
+ *    0-based; the same (seed, stream_id, r) always gives the same run, whatever
+ *    else shares the GPU.
+ *  - Outputs are replica-major: signs[r*n + i] in {-1, +1} (a state of exactly
+ *    zero reads as +1), energy[r] = H of replica r's signs.
+ *  - The caller owns every buffer it passes; the library copies what it keeps.
+ *  - Every path computes in the precision it names, on the GPU, in hand-written
+ *    kernels; there is no CPU fallback.  Without a usable CUDA device, calls
+ *    that need one return NMFA_ECUDA.
+ */
+#ifndef NMFA_H_
+#define NMFA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define NMFA_OK 0
+#define NMFA_EINVAL (-1)       /* bad argument (size, pointer, T <= 0, alpha, sigma) */
+#define NMFA_ENOTSYM (-2)      /* J is not symmetric */
+#define NMFA_EDIAG (-3)        /* J has a nonzero diagonal entry */
+#define NMFA_ENOMEM (-4)       /* device or host allocation failed */
+#define NMFA_ECUDA (-5)        /* CUDA runtime error (message has the details) */
+#define NMFA_ETIMEOUT (-6)     /* a bounded device-side wait gave up */
+#define NMFA_EUNSUPPORTED (-7) /* valid input this path cannot take (size, precision) */
+
+/* Storage and arithmetic of a problem (fixed at creation). */
+typedef enum {
+  NMFA_FP64 = 0,      /* FP64 CUDA-core path; coupling sums j-ascending, unfused */
+  NMFA_FP32 = 1,      /* FP32 CUDA-core path, one instance per launch */
+  NMFA_BF16 = 2,      /* tcgen05 tensor path: J and S in BF16, FP32 accumulation and
+                         FP32 master state; J must be exactly representable in BF16 */
+  NMFA_BF16_FP8J = 3  /* as NMFA_BF16 with J stored as FP8 E4M3 (exact values only) */
+} nmfa_precision;
+
+typedef struct nmfa_problem nmfa_problem; /* opaque; owns device copies of (h, J) */
+
+/*
+ * nmfa_create -- upload a dense Ising problem (Eq. (1)) and precompute, on the GPU in
+ * FP64, the row norms d_i = sqrt(h_i^2 + sum_j J_ij^2) of Algorithm 1 line 6
+ * (Sec. II: the root mean square of the terms acting on spin i).  A spin with
+ * d_i = 0 gets a normalised field of 0.
+ *   n         number of spins, 1 <= n <= 65536 (the CUDA-core paths accept less;
+ *             NMFA_EUNSUPPORTED when the state does not fit on chip)
+ *   h         host, n float64, or NULL for h = 0
+ *   J         host, n*n float64, row-major, symmetric, zero diagonal
+ *   precision an nmfa_precision value
+ *   out       receives the handle (NULL on failure)
+ * Checks (before any device work): n range, symmetry, diagonal, finiteness, and
+ * for NMFA_BF16 / NMFA_BF16_FP8J exact representability of every J_ij in BF16 /
+ * E4M3 (else NMFA_EUNSUPPORTED).
+ */
+int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision,
+                nmfa_problem** out);
+
+/*
+ * nmfa_create_csr -- the same problem given as CSR (sparse graphs, e.g. the
+ * degree-3 MAX-CUT instances of Sec. III).  row_ptr has n+1 int64 entries starting
+ * at 0; col/val have row_ptr[n] entries, columns strictly ascending within a row,
+ * in [0, n); the pattern and values must be symmetric with no diagonal entry.
+ * Coupling sums run over the stored entries in stored order.  Only NMFA_FP32 and
+ * NMFA_FP64 take CSR input (others: NMFA_EUNSUPPORTED).
+ */
+int nmfa_create_csr(int32_t n, const double* h, const int64_t* row_ptr,
+                    const int32_t* col, const double* val, int32_t precision,
+                    nmfa_problem** out);
+
+/* Frees the handle and its device memory (NULL is a no-op).  Waits for the
+ * handle's runs in flight to finish first. */
+void nmfa_destroy(nmfa_problem* p);
+
+/*
+ * nmfa_run -- Algorithm 1 end to end with HOST buffers: copies T to the device,
+ * runs t_f annealing steps for `replicas` replicas, reads out the signs, evaluates
+ * Eq. (1) on the GPU, copies the results back and returns when they are written.
+ *   T              host, t_f float64 temperatures T_1..T_tf, each > 0 (Fig. 2's
+ *                  schedule is an input; see the instance module for a default)
+ *   t_f            number of steps, >= 0 (0 reads out the initial zero state)
+ *   sigma          standard deviation of the Gaussian noise, >= 0 (Sec. II)
+ *   alpha          mixing constant, 0 < alpha <= 1 (Algorithm 1 line 10)
+ *   replicas       R >= 1
+ *   seed,stream_id select the noise stream (see the conventions above)
+ *   signs_out      host, R*n int8 (may be NULL)
+ *   energy_out     host, R float64 (may be NULL); exact for integer problems
+ *   energy_i64_out host, R int64 or NULL; only for problems whose h and J are all
+ *                  integers (else NMFA_EINVAL)
+ * Not reentrant per handle: runs on one handle are serialised on the device.
+ */
+int nmfa_run(nmfa_problem* p, const double* T, int32_t t_f, double sigma, double alpha,
+             int32_t replicas, uint64_t seed, uint32_t stream_id, int8_t* signs_out,
+             double* energy_out, int64_t* energy_i64_out);
+
+/*
+ * nmfa_run_device -- as nmfa_run with DEVICE pointers, enqueued on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream) and returning without
+ * synchronising.  T_dev holds t_f float64; signs_dev R*n int8, energy_dev R float64,
+ * energy_i64_dev R int64; any output may be NULL.  Device-side timeouts are reported
+ * by the next call on the handle or by nmfa_sync().  The handle's scratch memory
+ * (grown on demand, never shrunk) is reused; consecutive runs on one handle are
+ * ordered on the device even across streams.
+ */
+int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma,
+                    double alpha, int32_t replicas, uint64_t seed, uint32_t stream_id,
+                    int8_t* signs_dev, double* energy_dev, int64_t* energy_i64_dev,
+                    void* cuda_stream);
+
+/* Waits for the handle's last run and returns its device-side status
+ * (NMFA_OK or NMFA_ETIMEOUT) or a CUDA error. */
+int nmfa_sync(nmfa_problem* p);
+
+/*
+ * nmfa_debug_run -- test entry (not part of the stable ABI): nmfa_run_device with
+ * access to the continuous state, for the single-step and trajectory parity checks.
+ *   noise_sign  +1 (normal), 0 (noise off), -1 (every draw negated)
+ *   s0_dev      R*n float64 initial state, or NULL for Algorithm 1's s = 0
+ *   s_out_dev   R*n float64 final state s_i (before the sign readout), or NULL
+ *   phi_out_dev R*n float64 Phi_i of the last step, or NULL
+ * Other arguments as in nmfa_run_device.
+ */
+int nmfa_debug_run(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma,
+                   double alpha, int32_t replicas, uint64_t seed, uint32_t stream_id,
+                   int32_t noise_sign, const double* s0_dev, double* s_out_dev,
+                   double* phi_out_dev, int8_t* signs_dev, double* energy_dev,
+                   int64_t* energy_i64_dev, void* cuda_stream);
+
+/* Problem facts: spins, precision, 1 if h and J are integer-valued, device bytes
+ * held (any pointer may be NULL). */
+int nmfa_problem_info(const nmfa_problem* p, int32_t* n, int32_t* precision,
+                      int32_t* integer_valued, int64_t* device_bytes);
+
+/* Profiling: when enabled, each run records CUDA events around its annealing
+ * kernel(s) on the run's stream; nmfa_last_kernel_ms() then waits for the last run
+ * and returns the annealing-kernel time in milliseconds (energy kernel excluded). */
+int nmfa_profile_enable(nmfa_problem* p, int32_t on);
+int nmfa_last_kernel_ms(nmfa_problem* p, float* ms);
+
+/* Tuning of the CUDA-core paths: replicas held by one CTA (0 = automatic, else
+ * 1, 2, 4 or 8).  Results do not depend on it. */
+int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t replicas_per_cta);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t nmfa_launch_count(void);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* nmfa_last_error(void);
+
+/* Library version string. */
+const char* nmfa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMFA_H_ */

@@ -71,11 +71,11 @@ def _load():
         lib.orc_energy.restype = f64
         lib.orc_energy_i64.argtypes = [i32, P, P, P]
         lib.orc_energy_i64.restype = i64
-        lib.orc_run_dense.argtypes = [i32, P, P, P, i32, f64, f64, i32, u64, u32, i32,
-                                      P, P, P, P, i32]
+        lib.orc_run_dense.argtypes = [i32, P, P, P, i32, f64, f64, i32, i64, u64, u32,
+                                      i32, P, P, P, P, i32]
         lib.orc_run_dense.restype = ctypes.c_int
-        lib.orc_run_csr.argtypes = [i32, P, P, P, P, P, i32, f64, f64, i32, u64, u32,
-                                    i32, P, P, P, P, i32]
+        lib.orc_run_csr.argtypes = [i32, P, P, P, P, P, i32, f64, f64, i32, i64, u64,
+                                    u32, i32, P, P, P, P, i32]
         lib.orc_run_csr.restype = ctypes.c_int
         lib.orc_brute_force.argtypes = [i32, P, P, P, P]
         lib.orc_brute_force.restype = f64
@@ -141,8 +141,8 @@ def is_integer_problem(J, h=None) -> bool:
 
 
 def run(J, T, sigma, alpha, replicas, seed=0, stream=0, h=None, noise_sign=1, s0=None,
-        want_state=False, want_phi=False, nthreads=0, csr=None):
-    """Algorithm 1 over `replicas` replicas.  Returns a dict with
+        want_state=False, want_phi=False, nthreads=0, csr=None, r_first=0):
+    """Algorithm 1 over replicas r_first .. r_first+replicas-1.  Returns a dict with
     signs (R, n) int8, energy (R,) float64, energy_i64 (R,) int64 or None,
     and, on request, state (R, n) and phi (R, n) (the last step's Phi).
 
@@ -168,12 +168,12 @@ def run(J, T, sigma, alpha, replicas, seed=0, stream=0, h=None, noise_sign=1, s0
     phi = np.zeros((replicas, n)) if want_phi else None
     if csr is not None:
         rc = lib.orc_run_csr(n, _ptr(h), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(T),
-                             t_f, float(sigma), float(alpha), int(replicas), int(seed),
+                             t_f, float(sigma), float(alpha), int(replicas), int(r_first), int(seed),
                              int(stream), int(noise_sign), _ptr(s0), _ptr(state),
                              _ptr(phi), _ptr(signs), int(nthreads))
     else:
         rc = lib.orc_run_dense(n, _ptr(h), _ptr(J), _ptr(T), t_f, float(sigma),
-                               float(alpha), int(replicas), int(seed), int(stream),
+                               float(alpha), int(replicas), int(r_first), int(seed), int(stream),
                                int(noise_sign), _ptr(s0), _ptr(state), _ptr(phi),
                                _ptr(signs), int(nthreads))
     if rc != 0:

@@ -1,0 +1,586 @@
+// k_simt.cu -- CUDA-core NMFA kernels (FP32 and FP64), the Eq. (1) energy kernels
+// and the preparation kernels (row norms, storage conversion).
+//
+// Dense and CSR annealing use the same "replica-resident" design: one CTA owns a
+// block of `RC` replicas for ALL n spins, keeps their state s in shared memory
+// (two buffers: Algorithm 1 computes every Phi_i from the old state before any
+// s_i changes, lines 5-11), runs all t_f steps in one launch, and reads out the
+// signs at the end.  No CTA waits on another, so the launch needs no grid barrier.
+// Thread i computes Phi_i for the CTA's replicas; for symmetric J, row i equals
+// column i, so J[j*n + i] for fixed j is read coalesced across the warp.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "nmfa_device.cuh"
+#include "nmfa_internal.h"
+
+namespace nmfa {
+
+namespace {
+
+constexpr int kSimtThreads = 256;
+
+// Per-precision arithmetic.  The FP64 path reproduces Algorithm 1 in the order it
+// is written, with every product and sum rounded separately (no FMA), so that its
+// trajectories can be compared with an independent FP64 evaluation bit for bit
+// apart from the last-place differences of tanh/log/sin/cos.
+template <typename T>
+struct Arith;
+
+template <>
+struct Arith<float> {
+  static __device__ __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
+  static __device__ __forceinline__ float field(float P, double d, float inv_d) {
+    (void)d;
+    return P * inv_d;
+  }
+  static __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
+};
+
+template <>
+struct Arith<double> {
+  static __device__ __forceinline__ double mac(double acc, double a, double b) {
+    return __dadd_rn(acc, __dmul_rn(a, b));
+  }
+  static __device__ __forceinline__ double field(double P, double d, float inv_d) {
+    (void)inv_d;
+    return d > 0.0 ? __ddiv_rn(P, d) : 0.0;
+  }
+  static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+};
+
+// Draws for replicas r0..r0+RC-1 of spin i at step t (RC in {1, 2, 4, 8}; r0 is
+// a multiple of RC, so replica blocks never straddle a generator call unless
+// RC = 8, which takes two).
+template <typename T, int RC>
+__device__ __forceinline__ void draw(NoiseKey key, uint32_t stream, int r0, int t, int i,
+                                     T z[RC]) {
+  constexpr int G = (RC + 3) / 4;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const uint4 w = noise_words(key, stream, static_cast<uint32_t>((r0 >> 2) + g),
+                                static_cast<uint32_t>(t), static_cast<uint32_t>(i));
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = gauss4_f32(w);
+      const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int kk = g * 4 + k - (r0 & 3);
+        if (kk >= 0 && kk < RC) z[kk] = qq[k];
+      }
+    } else {
+      double qq[4];
+      gauss4_f64(w, qq);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int kk = g * 4 + k - (r0 & 3);
+        if (kk >= 0 && kk < RC) z[kk] = qq[k];
+      }
+    }
+  }
+}
+
+// The per-spin tail of a step shared by the dense and CSR kernels: normalise,
+// add noise, Boltzmann update (line 7) and alpha-mixing (line 10).
+template <typename T, int RC>
+__device__ __forceinline__ void finish_spin(const T acc[RC], int i, int t, int r0, int R,
+                                            int n, T hi, double di, float inv_di, T sigma,
+                                            T ns, T Tt, T inv_Tt, T alpha, T one_m_alpha,
+                                            const T* cur, T* nxt, NoiseKey key,
+                                            uint32_t stream, double* phi_out) {
+  T z[RC];
+  draw<T, RC>(key, stream, r0, t, i, z);
+#pragma unroll
+  for (int k = 0; k < RC; ++k) {
+    T phi, sh, s_new;
+    if constexpr (sizeof(T) == 8) {
+      const double P = __dadd_rn(hi, acc[k]);
+      const double f = Arith<double>::field(P, di, inv_di);
+      phi = __dadd_rn(f, __dmul_rn(__dmul_rn(sigma, z[k]), ns));
+      sh = -tanh(__ddiv_rn(phi, Tt));
+      s_new = __dadd_rn(__dmul_rn(alpha, sh), __dmul_rn(one_m_alpha, cur[i * RC + k]));
+      (void)inv_Tt;
+    } else {
+      const float P = hi + acc[k];
+      phi = fmaf(sigma * ns, z[k], P * inv_di);
+      sh = -tanhf(phi * inv_Tt);
+      s_new = fmaf(alpha, sh, one_m_alpha * cur[i * RC + k]);
+      (void)Tt;
+      (void)di;
+    }
+    nxt[i * RC + k] = s_new;
+    const int r = r0 + k;
+    if (phi_out != nullptr && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(phi);
+  }
+}
+
+template <typename T, int RC>
+__device__ __forceinline__ void init_state(T* S, int n, int r0, int R, const double* s0) {
+  for (int idx = threadIdx.x; idx < n * RC; idx += blockDim.x) {
+    const int i = idx / RC, k = idx % RC, r = r0 + k;
+    S[idx] = (s0 != nullptr && r < R) ? static_cast<T>(s0[static_cast<int64_t>(r) * n + i]) : T(0);
+  }
+}
+
+template <typename T, int RC>
+__device__ __forceinline__ void readout(const T* S, int n, int r0, int R, int8_t* signs,
+                                        double* s_out) {
+  for (int idx = threadIdx.x; idx < n * RC; idx += blockDim.x) {
+    const int k = idx / n, i = idx % n, r = r0 + k;  // i fastest: coalesced writes
+    if (r >= R) continue;
+    const T s = S[i * RC + k];
+    signs[static_cast<int64_t>(r) * n + i] = (s >= T(0)) ? int8_t(1) : int8_t(-1);
+    if (s_out != nullptr) s_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(s);
+  }
+}
+
+template <typename T, int RC, bool J_SMEM>
+__global__ void __launch_bounds__(kSimtThreads)
+dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = pb.n;
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + n * RC;
+  T* Jsm = S1 + n * RC;
+  const T* Jg = static_cast<const T*>(pb.J);
+  const T* hv = static_cast<const T*>(pb.h);
+  const int r0 = blockIdx.x * RC;
+  const int R = rp.replicas;
+  if constexpr (J_SMEM) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Jsm[idx] = Jg[idx];
+  }
+  const T* J = J_SMEM ? Jsm : Jg;
+  init_state<T, RC>(S0, n, r0, R, rp.s0);
+  __syncthreads();
+  const NoiseKey key = make_noise_key(rp.seed);
+  const T sigma = static_cast<T>(rp.sigma), ns = static_cast<T>(rp.noise_sign);
+  const T alpha = static_cast<T>(rp.alpha), oma = static_cast<T>(1.0 - rp.alpha);
+  T* cur = S0;
+  T* nxt = S1;
+  for (int t = 0; t < rp.t_f; ++t) {
+    const double Td = rp.T[t];
+    const T Tt = static_cast<T>(Td);
+    const T inv_Tt = static_cast<T>(1.0 / Td);
+    double* phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      T acc[RC];
+#pragma unroll
+      for (int k = 0; k < RC; ++k) acc[k] = T(0);
+      const T* col = J + i;
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) {
+        const T jv = J_SMEM ? col[static_cast<int64_t>(j) * n] : __ldg(col + static_cast<int64_t>(j) * n);
+        const T* sj = cur + j * RC;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) acc[k] = Arith<T>::mac(acc[k], jv, sj[k]);
+      }
+      finish_spin<T, RC>(acc, i, t, r0, R, n, hv[i], pb.d[i], pb.inv_d32[i], sigma, ns, Tt,
+                         inv_Tt, alpha, oma, cur, nxt, key, rp.stream_id, phi_out);
+    }
+    __syncthreads();
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  readout<T, RC>(cur, n, r0, R, rp.signs, rp.s_out);
+}
+
+// CSR: coupling sums run over the stored entries of row i in stored order.
+template <typename T, int RC, typename VT>
+__global__ void __launch_bounds__(kSimtThreads)
+csr_kernel(CsrProblem pb, RunParams rp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = pb.n;
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* S1 = S0 + n * RC;
+  const VT* val = static_cast<const VT*>(pb.val);
+  const T* hv = static_cast<const T*>(pb.h);
+  const int r0 = blockIdx.x * RC;
+  const int R = rp.replicas;
+  init_state<T, RC>(S0, n, r0, R, rp.s0);
+  __syncthreads();
+  const NoiseKey key = make_noise_key(rp.seed);
+  const T sigma = static_cast<T>(rp.sigma), ns = static_cast<T>(rp.noise_sign);
+  const T alpha = static_cast<T>(rp.alpha), oma = static_cast<T>(1.0 - rp.alpha);
+  T* cur = S0;
+  T* nxt = S1;
+  for (int t = 0; t < rp.t_f; ++t) {
+    const double Td = rp.T[t];
+    const T Tt = static_cast<T>(Td);
+    const T inv_Tt = static_cast<T>(1.0 / Td);
+    double* phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      T acc[RC];
+#pragma unroll
+      for (int k = 0; k < RC; ++k) acc[k] = T(0);
+      const int kb = __ldg(pb.row_ptr + i), ke = __ldg(pb.row_ptr + i + 1);
+      for (int q = kb; q < ke; ++q) {
+        const int j = __ldg(pb.col + q);
+        const T v = static_cast<T>(__ldg(val + q));
+        const T* sj = cur + j * RC;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) acc[k] = Arith<T>::mac(acc[k], v, sj[k]);
+      }
+      finish_spin<T, RC>(acc, i, t, r0, R, n, hv[i], pb.d[i], pb.inv_d32[i], sigma, ns, Tt,
+                         inv_Tt, alpha, oma, cur, nxt, key, rp.stream_id, phi_out);
+    }
+    __syncthreads();
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  readout<T, RC>(cur, n, r0, R, rp.signs, rp.s_out);
+}
+
+int max_smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+  }
+  return v;
+}
+
+template <typename T, int RC>
+int launch_dense_rc(const DenseSimtProblem& pb, const RunParams& rp, cudaStream_t st) {
+  const size_t state_bytes = 2ull * pb.n * RC * sizeof(T);
+  const size_t j_bytes = static_cast<size_t>(pb.n) * pb.n * sizeof(T);
+  const int limit = max_smem_optin();
+  const int grid = (rp.replicas + RC - 1) / RC;
+  if (state_bytes + j_bytes <= static_cast<size_t>(limit) && pb.n <= 128) {
+    auto k = dense_simt_kernel<T, RC, true>;
+    const size_t smem = state_bytes + j_bytes;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    k<<<grid, kSimtThreads, smem, st>>>(pb, rp);
+  } else {
+    if (state_bytes > static_cast<size_t>(limit))
+      return set_error(NMFA_EUNSUPPORTED, "dense CUDA-core path: state of n spins does not fit in shared memory");
+    auto k = dense_simt_kernel<T, RC, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
+    k<<<grid, kSimtThreads, state_bytes, st>>>(pb, rp);
+  }
+  count_launch();
+  return cuda_error(cudaGetLastError(), "dense CUDA-core kernel launch");
+}
+
+template <typename T, int RC>
+int launch_csr_rc(const CsrProblem& pb, const RunParams& rp, cudaStream_t st) {
+  const size_t state_bytes = 2ull * pb.n * RC * sizeof(T);
+  if (state_bytes > static_cast<size_t>(max_smem_optin()))
+    return set_error(NMFA_EUNSUPPORTED, "CSR path: state of n spins does not fit in shared memory");
+  const int grid = (rp.replicas + RC - 1) / RC;
+  if (pb.val_int8) {
+    auto k = csr_kernel<T, RC, int8_t>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
+    k<<<grid, kSimtThreads, state_bytes, st>>>(pb, rp);
+  } else {
+    auto k = csr_kernel<T, RC, T>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
+    k<<<grid, kSimtThreads, state_bytes, st>>>(pb, rp);
+  }
+  count_launch();
+  return cuda_error(cudaGetLastError(), "CSR kernel launch");
+}
+
+// Largest replica block (of 1, 2, 4, 8) whose double-buffered state fits, but no
+// larger than needed to give every SM work.
+int pick_rc(int n, int replicas, size_t elem, int requested) {
+  if (requested > 0) return requested;
+  int sms = 148;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t limit = static_cast<size_t>(max_smem_optin());
+  int rc = 8;
+  while (rc > 1 && 2ull * n * rc * elem > limit) rc >>= 1;
+  while (rc > 1 && (replicas + rc - 1) / rc < sms) rc >>= 1;
+  return rc;
+}
+
+}  // namespace
+
+int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
+                      cudaStream_t st, int replicas_per_cta) {
+  const int rc = pick_rc(pb.n, rp.replicas, fp64 ? 8 : 4, replicas_per_cta);
+  if (fp64) {
+    switch (rc) {
+      case 1: return launch_dense_rc<double, 1>(pb, rp, st);
+      case 2: return launch_dense_rc<double, 2>(pb, rp, st);
+      case 4: return launch_dense_rc<double, 4>(pb, rp, st);
+      default: return launch_dense_rc<double, 8>(pb, rp, st);
+    }
+  }
+  switch (rc) {
+    case 1: return launch_dense_rc<float, 1>(pb, rp, st);
+    case 2: return launch_dense_rc<float, 2>(pb, rp, st);
+    case 4: return launch_dense_rc<float, 4>(pb, rp, st);
+    default: return launch_dense_rc<float, 8>(pb, rp, st);
+  }
+}
+
+int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,
+               int replicas_per_cta) {
+  const int rc = pick_rc(pb.n, rp.replicas, fp64 ? 8 : 4, replicas_per_cta);
+  if (fp64) {
+    switch (rc) {
+      case 1: return launch_csr_rc<double, 1>(pb, rp, st);
+      case 2: return launch_csr_rc<double, 2>(pb, rp, st);
+      case 4: return launch_csr_rc<double, 4>(pb, rp, st);
+      default: return launch_csr_rc<double, 8>(pb, rp, st);
+    }
+  }
+  switch (rc) {
+    case 1: return launch_csr_rc<float, 1>(pb, rp, st);
+    case 2: return launch_csr_rc<float, 2>(pb, rp, st);
+    case 4: return launch_csr_rc<float, 4>(pb, rp, st);
+    default: return launch_csr_rc<float, 8>(pb, rp, st);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Eq. (1) energies.  H_r = (1/2) sum_i s_i (sum_j J_ij s_j) + sum_i h_i s_i, which
+// equals the unordered-pair sum for symmetric J with zero diagonal.  Integer
+// problems are summed exactly (int32 row sums, int64 totals); real-valued ones
+// in FP64.  One CTA per block of kEnergyReps replicas.
+// ----------------------------------------------------------------------------
+constexpr int kEnergyReps = 8;
+constexpr int kEnergyThreads = 256;
+
+__device__ __forceinline__ int dp4a_s8(int a, int b, int c) { return __dp4a(a, b, c); }
+
+// Integer J (int8, rows padded to ld8 bytes, a multiple of 16): one warp per row
+// i, lanes stride over j in 16-byte words, dp4a products.
+__global__ void __launch_bounds__(kEnergyThreads)
+energy_int8_kernel(int n, int ld8, const int8_t* __restrict__ J8, const double* __restrict__ h,
+                   const int8_t* __restrict__ signs, int R, double* E, long long* Ei64) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int8_t* sg = reinterpret_cast<int8_t*>(smem_raw);  // [kEnergyReps][ld8]
+  __shared__ long long part[kEnergyThreads / 32][kEnergyReps];
+  const int r0 = blockIdx.x * kEnergyReps;
+  for (int idx = threadIdx.x; idx < kEnergyReps * ld8; idx += blockDim.x) {
+    const int k = idx / ld8, j = idx % ld8, r = r0 + k;
+    sg[idx] = (r < R && j < n) ? signs[static_cast<int64_t>(r) * n + j] : int8_t(0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  long long acc[kEnergyReps];
+#pragma unroll
+  for (int k = 0; k < kEnergyReps; ++k) acc[k] = 0;
+  const int words = ld8 / 16;
+  for (int i = warp; i < n; i += blockDim.x >> 5) {
+    int f[kEnergyReps];
+#pragma unroll
+    for (int k = 0; k < kEnergyReps; ++k) f[k] = 0;
+    const int4* row = reinterpret_cast<const int4*>(J8 + static_cast<int64_t>(i) * ld8);
+    for (int w = lane; w < words; w += 32) {
+      const int4 jv = __ldg(row + w);
+#pragma unroll
+      for (int k = 0; k < kEnergyReps; ++k) {
+        const int4 sv = reinterpret_cast<const int4*>(sg + k * ld8)[w];
+        f[k] = dp4a_s8(jv.x, sv.x, f[k]);
+        f[k] = dp4a_s8(jv.y, sv.y, f[k]);
+        f[k] = dp4a_s8(jv.z, sv.z, f[k]);
+        f[k] = dp4a_s8(jv.w, sv.w, f[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEnergyReps; ++k) {
+      int v = f[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) acc[k] += static_cast<long long>(v) * sg[k * ld8 + i];
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kEnergyReps; ++k) part[warp][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kEnergyReps) {
+    const int k = threadIdx.x, r = r0 + k;
+    if (r < R) {
+      long long pairs2 = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pairs2 += part[w][k];
+      long long field = 0;
+      if (h != nullptr)
+        for (int i = 0; i < n; ++i) field += static_cast<long long>(h[i]) * sg[k * ld8 + i];
+      const long long H = pairs2 / 2 + field;
+      if (Ei64 != nullptr) Ei64[r] = H;
+      if (E != nullptr) E[r] = static_cast<double>(H);
+    }
+  }
+}
+
+// Real-valued (or wide-integer) J in FP64; thread per row i, j ascending, or CSR.
+__global__ void __launch_bounds__(kEnergyThreads)
+energy_f64_kernel(int n, const double* __restrict__ J64, const int32_t* __restrict__ row_ptr,
+                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                  const double* __restrict__ h, const int8_t* __restrict__ signs, int R,
+                  int integer_valued, double* E, long long* Ei64) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int8_t* sg = reinterpret_cast<int8_t*>(smem_raw);  // [kEnergyReps][n]
+  __shared__ double part[kEnergyThreads][kEnergyReps];
+  const int r0 = blockIdx.x * kEnergyReps;
+  for (int idx = threadIdx.x; idx < kEnergyReps * n; idx += blockDim.x) {
+    const int k = idx / n, j = idx % n, r = r0 + k;
+    sg[idx] = (r < R) ? signs[static_cast<int64_t>(r) * n + j] : int8_t(0);
+  }
+  __syncthreads();
+  double acc[kEnergyReps];
+#pragma unroll
+  for (int k = 0; k < kEnergyReps; ++k) acc[k] = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double f[kEnergyReps];
+#pragma unroll
+    for (int k = 0; k < kEnergyReps; ++k) f[k] = 0.0;
+    if (row_ptr != nullptr) {
+      for (int q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+        const double v = val[q];
+        const int j = col[q];
+#pragma unroll
+        for (int k = 0; k < kEnergyReps; ++k) f[k] += v * sg[k * n + j];
+      }
+    } else {
+      for (int j = 0; j < n; ++j) {
+        const double v = __ldg(J64 + static_cast<int64_t>(j) * n + i);
+#pragma unroll
+        for (int k = 0; k < kEnergyReps; ++k) f[k] += v * sg[k * n + j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kEnergyReps; ++k) acc[k] += f[k] * sg[k * n + i];
+  }
+#pragma unroll
+  for (int k = 0; k < kEnergyReps; ++k) part[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < kEnergyReps) {
+    const int k = threadIdx.x, r = r0 + k;
+    if (r < R) {
+      double pairs2 = 0.0;
+      for (int w = 0; w < (int)blockDim.x; ++w) pairs2 += part[w][k];
+      double field = 0.0;
+      if (h != nullptr)
+        for (int i = 0; i < n; ++i) field += h[i] * sg[k * n + i];
+      const double H = 0.5 * pairs2 + field;
+      if (E != nullptr) E[r] = H;
+      if (Ei64 != nullptr && integer_valued) Ei64[r] = static_cast<long long>(llrint(H));
+    }
+  }
+}
+
+int launch_energy(const EnergyProblem& ep, const int8_t* signs, int32_t replicas, double* energy,
+                  int64_t* energy_i64, cudaStream_t st) {
+  if (energy == nullptr && energy_i64 == nullptr) return NMFA_OK;
+  const int grid = (replicas + kEnergyReps - 1) / kEnergyReps;
+  if (ep.J8 != nullptr) {
+    const int ld8 = (ep.n + 15) / 16 * 16;
+    const size_t smem = static_cast<size_t>(kEnergyReps) * ld8;
+    if (smem > static_cast<size_t>(max_smem_optin()))
+      return set_error(NMFA_EUNSUPPORTED, "energy kernel: sign block does not fit in shared memory");
+    cudaFuncSetAttribute(energy_int8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    energy_int8_kernel<<<grid, kEnergyThreads, smem, st>>>(
+        ep.n, ld8, ep.J8, ep.h, signs, replicas, energy, reinterpret_cast<long long*>(energy_i64));
+  } else {
+    const size_t smem = static_cast<size_t>(kEnergyReps) * ep.n;
+    if (smem > static_cast<size_t>(max_smem_optin()) - static_cast<size_t>(kEnergyThreads) * kEnergyReps * 8)
+      return set_error(NMFA_EUNSUPPORTED, "energy kernel: sign block does not fit in shared memory");
+    cudaFuncSetAttribute(energy_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    energy_f64_kernel<<<grid, kEnergyThreads, smem, st>>>(
+        ep.n, ep.J64, ep.row_ptr, ep.col, ep.val64, ep.h, signs, replicas,
+        ep.integer_valued ? 1 : 0, energy, reinterpret_cast<long long*>(energy_i64));
+  }
+  count_launch();
+  return cuda_error(cudaGetLastError(), "energy kernel launch");
+}
+
+// ----------------------------------------------------------------------------
+// Preparation (Algorithm 1 line 6 denominators, computed once per problem in
+// FP64): d_i = sqrt(h_i^2 + sum_j J_ij^2), sum over j ascending, unfused.
+// ----------------------------------------------------------------------------
+__global__ void row_norms_dense_kernel(int n, const double* __restrict__ J64,
+                                       const double* __restrict__ h, double* d, float* inv_d32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double v = J64[static_cast<int64_t>(j) * n + i];  // = J[i][j] by symmetry
+    acc = __dadd_rn(acc, __dmul_rn(v, v));
+  }
+  const double hi = h != nullptr ? h[i] : 0.0;
+  const double di = __dsqrt_rn(__dadd_rn(__dmul_rn(hi, hi), acc));
+  d[i] = di;
+  inv_d32[i] = di > 0.0 ? static_cast<float>(1.0 / di) : 0.0f;
+}
+
+__global__ void row_norms_csr_kernel(int n, const int32_t* __restrict__ row_ptr,
+                                     const double* __restrict__ val, const double* __restrict__ h,
+                                     double* d, float* inv_d32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int q = row_ptr[i]; q < row_ptr[i + 1]; ++q) acc = __dadd_rn(acc, __dmul_rn(val[q], val[q]));
+  const double hi = h != nullptr ? h[i] : 0.0;
+  const double di = __dsqrt_rn(__dadd_rn(__dmul_rn(hi, hi), acc));
+  d[i] = di;
+  inv_d32[i] = di > 0.0 ? static_cast<float>(1.0 / di) : 0.0f;
+}
+
+__device__ __forceinline__ void store_kind(void* dst, int64_t idx, double v, int kind) {
+  switch (kind) {
+    case 0: static_cast<float*>(dst)[idx] = static_cast<float>(v); break;
+    case 1: static_cast<__nv_bfloat16*>(dst)[idx] = __double2bfloat16(v); break;
+    case 2: static_cast<__nv_fp8_storage_t*>(dst)[idx] = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3); break;
+    default: static_cast<int8_t*>(dst)[idx] = static_cast<int8_t>(v); break;
+  }
+}
+
+__global__ void convert_dense_kernel(int n, const double* __restrict__ J64, void* dst, int kind,
+                                     int64_t rows, int64_t ld) {
+  const int64_t total = rows * ld;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / ld, j = idx % ld;
+    const double v = (i < n && j < n) ? J64[i * n + j] : 0.0;
+    store_kind(dst, idx, v, kind);
+  }
+}
+
+__global__ void convert_vec_kernel(int n, const double* __restrict__ src, void* dst, int kind) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) store_kind(dst, i, src != nullptr ? src[i] : 0.0, kind);
+}
+
+int launch_row_norms_dense(int32_t n, const double* J64, const double* h, double* d, float* inv_d32,
+                           cudaStream_t st) {
+  row_norms_dense_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, J64, h, d, inv_d32);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "row norm kernel launch");
+}
+
+int launch_row_norms_csr(int32_t n, const int32_t* row_ptr, const double* val64, const double* h,
+                         double* d, float* inv_d32, cudaStream_t st) {
+  row_norms_csr_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, val64, h, d, inv_d32);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "row norm kernel launch");
+}
+
+int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int64_t rows, int64_t ld,
+                         cudaStream_t st) {
+  const int64_t total = rows * ld;
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4096));
+  convert_dense_kernel<<<std::max(grid, 1), 256, 0, st>>>(n, J64, dst, kind, rows, ld);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "conversion kernel launch");
+}
+
+int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st) {
+  convert_vec_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst, kind);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "conversion kernel launch");
+}
+
+}  // namespace nmfa

@@ -1,0 +1,599 @@
+// nmfa_api.cu -- the C ABI of libnmfa.so (declared in include/nmfa.h): argument
+// checking, device copies of (h, J) in the storage each path needs, the per-handle
+// scratch workspace, run orchestration on the caller's stream, and error codes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "nmfa_internal.h"
+
+namespace nmfa {
+
+std::atomic<uint64_t> g_launches{0};
+
+static thread_local std::string t_last_error;
+
+int set_error(int code, const std::string& msg) {
+  t_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return NMFA_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(NMFA_ENOMEM, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  return set_error(NMFA_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace nmfa
+
+using namespace nmfa;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct nmfa_problem {
+  int32_t n = 0;
+  int32_t precision = 0;
+  bool csr = false;
+  bool integer_valued = false;
+  bool int8_ok = false;  // integer problem with |J| <= 127: int8 energy copy
+  int32_t nnz = 0;
+  int32_t n_pad = 0;
+  int device = 0;
+  // device copies
+  double* J64 = nullptr;
+  double* h64 = nullptr;
+  double* d64 = nullptr;
+  float* inv_d32 = nullptr;
+  float* h32 = nullptr;
+  float* J32 = nullptr;
+  void* Jq = nullptr;      // bf16 / e4m3 padded
+  int8_t* J8 = nullptr;    // energy copy, rows padded to 16 bytes
+  int32_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  int8_t* val8 = nullptr;
+  bool val_is_int8 = false;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocations;
+  // scratch
+  DevBuf ws;              // kernel scratch (tensor path)
+  DevBuf io;              // host-API staging: T, signs, energies
+  DevBuf sign_scratch;    // signs when the caller does not want them
+  int32_t* status = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t prof0 = nullptr, prof1 = nullptr;
+  bool profiling = false;
+  bool prof_valid = false;
+  int replicas_per_cta = 0;  // CUDA-core paths: 0 = automatic
+  std::mutex mu;
+};
+
+namespace {
+
+int dev_alloc(nmfa_problem* p, void** out, size_t bytes) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return cuda_error(e, "cudaMalloc");
+  }
+  p->allocations.push_back(*out);
+  p->device_bytes += static_cast<int64_t>(bytes);
+  return NMFA_OK;
+}
+
+template <typename T>
+int dev_alloc_t(nmfa_problem* p, T** out, size_t count) {
+  void* v = nullptr;
+  int rc = dev_alloc(p, &v, count * sizeof(T));
+  *out = static_cast<T*>(v);
+  return rc;
+}
+
+int ensure_buf(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p != nullptr) return NMFA_OK;
+  if (b.p != nullptr) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return cuda_error(e, "scratch cudaMalloc");
+  }
+  b.bytes = std::max<size_t>(bytes, 256);
+  return NMFA_OK;
+}
+
+bool bf16_exact(double v) {
+  const float f = static_cast<float>(v);
+  if (static_cast<double>(f) != v) return false;
+  uint32_t bits;
+  std::memcpy(&bits, &f, 4);
+  return (bits & 0xFFFFu) == 0u;
+}
+
+// All finite E4M3 values (bias 7, 3 mantissa bits, no infinities; S.1111.111 is NaN).
+bool e4m3_exact(double v) {
+  static std::vector<double> table = [] {
+    std::vector<double> t;
+    for (int b = 0; b < 256; ++b) {
+      const int sgn = (b >> 7) & 1, ex = (b >> 3) & 15, man = b & 7;
+      if (ex == 15 && man == 7) continue;
+      double mag = (ex == 0) ? std::ldexp(static_cast<double>(man), -9)
+                             : std::ldexp(1.0 + man / 8.0, ex - 7);
+      t.push_back(sgn ? -mag : mag);
+    }
+    return t;
+  }();
+  for (double x : table)
+    if (x == v) return true;
+  return false;
+}
+
+int validate_common(int32_t n, int32_t precision) {
+  if (n < 1 || n > 65536) return set_error(NMFA_EINVAL, "n must be in [1, 65536]");
+  if (precision < NMFA_FP64 || precision > NMFA_BF16_FP8J)
+    return set_error(NMFA_EINVAL, "unknown precision");
+  return NMFA_OK;
+}
+
+int check_device() {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return set_error(NMFA_ECUDA, "no CUDA device available");
+  }
+  return NMFA_OK;
+}
+
+int finish_create(nmfa_problem* p, const double* h) {
+  int rc;
+  if ((rc = cuda_error(cudaGetDevice(&p->device), "cudaGetDevice"))) return rc;
+  if ((rc = cuda_error(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking), "stream")))
+    return rc;
+  if ((rc = cuda_error(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming), "event")))
+    return rc;
+  if ((rc = cuda_error(cudaEventCreate(&p->prof0), "event"))) return rc;
+  if ((rc = cuda_error(cudaEventCreate(&p->prof1), "event"))) return rc;
+  if ((rc = dev_alloc_t(p, &p->status, 4))) return rc;
+  cudaStream_t st = p->own_stream;
+  const int n = p->n;
+  if ((rc = dev_alloc_t(p, &p->d64, n))) return rc;
+  if ((rc = dev_alloc_t(p, &p->inv_d32, std::max(n, p->n_pad)))) return rc;
+  if ((rc = dev_alloc_t(p, &p->h64, n))) return rc;
+  if (h != nullptr) {
+    if ((rc = cuda_error(cudaMemcpyAsync(p->h64, h, sizeof(double) * n, cudaMemcpyHostToDevice, st), "h upload")))
+      return rc;
+  } else {
+    if ((rc = cuda_error(cudaMemsetAsync(p->h64, 0, sizeof(double) * n, st), "h clear"))) return rc;
+  }
+  // h in binary32, zero-padded to n_pad for the tensor path's padded rows
+  if ((rc = dev_alloc_t(p, &p->h32, std::max(n, p->n_pad)))) return rc;
+  if ((rc = cuda_error(cudaMemsetAsync(p->h32, 0, sizeof(float) * std::max(n, p->n_pad), st), "h clear"))) return rc;
+  if ((rc = cuda_error(cudaMemsetAsync(p->inv_d32, 0, sizeof(float) * std::max(n, p->n_pad), st), "norm clear")))
+    return rc;
+  if ((rc = launch_convert_vec(n, p->h64, p->h32, 0, st))) return rc;
+  if (p->csr) {
+    if ((rc = launch_row_norms_csr(n, p->row_ptr, p->val64, p->h64, p->d64, p->inv_d32, st))) return rc;
+  } else {
+    if ((rc = launch_row_norms_dense(n, p->J64, p->h64, p->d64, p->inv_d32, st))) return rc;
+  }
+  if ((rc = cuda_error(cudaMemsetAsync(p->status, 0, 4, st), "status clear"))) return rc;
+  return cuda_error(cudaStreamSynchronize(st), "create");
+}
+
+void free_problem(nmfa_problem* p) {
+  if (p == nullptr) return;
+  if (p->done) cudaEventSynchronize(p->done);
+  for (void* a : p->allocations) cudaFree(a);
+  if (p->ws.p) cudaFree(p->ws.p);
+  if (p->io.p) cudaFree(p->io.p);
+  if (p->sign_scratch.p) cudaFree(p->sign_scratch.p);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->prof0) cudaEventDestroy(p->prof0);
+  if (p->prof1) cudaEventDestroy(p->prof1);
+  if (p->own_stream) cudaStreamDestroy(p->own_stream);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nmfa_last_error(void) { return t_last_error.c_str(); }
+
+const char* nmfa_version(void) { return "nmfa-gb300 0.1 (sm_103a)"; }
+
+uint64_t nmfa_launch_count(void) { return g_launches.load(); }
+
+int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, nmfa_problem** out) {
+  if (out == nullptr) return set_error(NMFA_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_common(n, precision);
+  if (rc) return rc;
+  if (J == nullptr) return set_error(NMFA_EINVAL, "J is NULL");
+  bool integer = true, int8_ok = true, bf16_ok = true, e4m3_ok = true;
+  for (int32_t i = 0; i < n; ++i) {
+    if (h != nullptr) {
+      if (!std::isfinite(h[i])) return set_error(NMFA_EINVAL, "h has a non-finite entry");
+      if (h[i] != std::nearbyint(h[i]) || std::fabs(h[i]) >= 2147483648.0) integer = false;
+    }
+    if (J[static_cast<int64_t>(i) * n + i] != 0.0) return set_error(NMFA_EDIAG, "J has a nonzero diagonal entry");
+    for (int32_t j = 0; j < n; ++j) {
+      const double v = J[static_cast<int64_t>(i) * n + j];
+      if (!std::isfinite(v)) return set_error(NMFA_EINVAL, "J has a non-finite entry");
+      if (j > i && v != J[static_cast<int64_t>(j) * n + i]) return set_error(NMFA_ENOTSYM, "J is not symmetric");
+      if (v != std::nearbyint(v) || std::fabs(v) >= 2147483648.0) integer = false;
+      if (std::fabs(v) > 127.0) int8_ok = false;
+    }
+  }
+  int8_ok = int8_ok && integer && static_cast<int64_t>(n) * 127 < (1ll << 30);
+  if (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) {
+    for (int64_t q = 0; q < static_cast<int64_t>(n) * n; ++q) {
+      if (precision == NMFA_BF16 && bf16_ok && !bf16_exact(J[q])) bf16_ok = false;
+      if (precision == NMFA_BF16_FP8J && e4m3_ok && !e4m3_exact(J[q])) e4m3_ok = false;
+    }
+    if (precision == NMFA_BF16 && !bf16_ok)
+      return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in BF16");
+    if (precision == NMFA_BF16_FP8J && !e4m3_ok)
+      return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in FP8 E4M3");
+  }
+  if ((rc = check_device())) return rc;
+  nmfa_problem* p = new nmfa_problem();
+  p->n = n;
+  p->precision = precision;
+  p->integer_valued = integer;
+  p->int8_ok = int8_ok;
+  p->n_pad = (n + 127) / 128 * 128;
+  cudaStream_t st = nullptr;
+  auto fail = [&](int code) {
+    std::string msg = t_last_error;
+    free_problem(p);
+    t_last_error = msg;
+    return code;
+  };
+  if ((rc = dev_alloc_t(p, &p->J64, static_cast<size_t>(n) * n))) return fail(rc);
+  if ((rc = cuda_error(cudaMemcpy(p->J64, J, sizeof(double) * n * static_cast<size_t>(n), cudaMemcpyHostToDevice), "J upload")))
+    return fail(rc);
+  if ((rc = finish_create(p, h))) return fail(rc);
+  st = p->own_stream;
+  if (precision == NMFA_FP32) {
+    if ((rc = dev_alloc_t(p, &p->J32, static_cast<size_t>(n) * n))) return fail(rc);
+    if ((rc = launch_convert_dense(n, p->J64, p->J32, 0, n, n, st))) return fail(rc);
+  } else if (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) {
+    const size_t elem = precision == NMFA_BF16 ? 2 : 1;
+    void* q = nullptr;
+    if ((rc = dev_alloc(p, &q, elem * p->n_pad * static_cast<size_t>(p->n_pad)))) return fail(rc);
+    p->Jq = q;
+    if ((rc = launch_convert_dense(n, p->J64, p->Jq, precision == NMFA_BF16 ? 1 : 2, p->n_pad, p->n_pad, st)))
+      return fail(rc);
+  }
+  if (int8_ok) {
+    const int64_t ld8 = (n + 15) / 16 * 16;
+    if ((rc = dev_alloc_t(p, &p->J8, static_cast<size_t>(n) * ld8))) return fail(rc);
+    if ((rc = launch_convert_dense(n, p->J64, p->J8, 3, n, ld8, st))) return fail(rc);
+  }
+  if ((rc = cuda_error(cudaStreamSynchronize(st), "create conversions"))) return fail(rc);
+  *out = p;
+  return NMFA_OK;
+}
+
+int nmfa_create_csr(int32_t n, const double* h, const int64_t* row_ptr, const int32_t* col,
+                    const double* val, int32_t precision, nmfa_problem** out) {
+  if (out == nullptr) return set_error(NMFA_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_common(n, precision);
+  if (rc) return rc;
+  if (precision != NMFA_FP32 && precision != NMFA_FP64)
+    return set_error(NMFA_EUNSUPPORTED, "CSR input takes NMFA_FP32 or NMFA_FP64 only");
+  if (row_ptr == nullptr) return set_error(NMFA_EINVAL, "row_ptr is NULL");
+  if (row_ptr[0] != 0) return set_error(NMFA_EINVAL, "row_ptr[0] must be 0");
+  const int64_t nnz = row_ptr[n];
+  if (nnz < 0 || nnz > (1ll << 31) - 1) return set_error(NMFA_EINVAL, "bad nnz");
+  if (nnz > 0 && (col == nullptr || val == nullptr)) return set_error(NMFA_EINVAL, "col/val is NULL");
+  bool integer = true, int8_ok = true;
+  for (int32_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return set_error(NMFA_EINVAL, "row_ptr is not monotone");
+    if (h != nullptr) {
+      if (!std::isfinite(h[i])) return set_error(NMFA_EINVAL, "h has a non-finite entry");
+      if (h[i] != std::nearbyint(h[i]) || std::fabs(h[i]) >= 2147483648.0) integer = false;
+    }
+    for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+      const int32_t j = col[q];
+      if (j < 0 || j >= n) return set_error(NMFA_EINVAL, "column index out of range");
+      if (q > row_ptr[i] && col[q - 1] >= j) return set_error(NMFA_EINVAL, "columns must ascend within a row");
+      if (j == i) return set_error(NMFA_EDIAG, "CSR has a diagonal entry");
+      const double v = val[q];
+      if (!std::isfinite(v)) return set_error(NMFA_EINVAL, "val has a non-finite entry");
+      if (v != std::nearbyint(v) || std::fabs(v) >= 2147483648.0) integer = false;
+      if (std::fabs(v) > 127.0) int8_ok = false;
+      // symmetric: find (j, i) by binary search in row j
+      const int32_t* b = col + row_ptr[j];
+      const int32_t* e = col + row_ptr[j + 1];
+      const int32_t* f = std::lower_bound(b, e, i);
+      if (f == e || *f != i || val[row_ptr[j] + (f - b)] != v) return set_error(NMFA_ENOTSYM, "CSR J is not symmetric");
+    }
+  }
+  if ((rc = check_device())) return rc;
+  nmfa_problem* p = new nmfa_problem();
+  p->n = n;
+  p->precision = precision;
+  p->csr = true;
+  p->nnz = static_cast<int32_t>(nnz);
+  p->integer_valued = integer;
+  p->int8_ok = false;  // energies of CSR problems use the CSR form
+  p->val_is_int8 = integer && int8_ok;
+  p->n_pad = n;
+  auto fail = [&](int code) {
+    std::string msg = t_last_error;
+    free_problem(p);
+    t_last_error = msg;
+    return code;
+  };
+  std::vector<int32_t> rp32(n + 1);
+  for (int32_t i = 0; i <= n; ++i) rp32[i] = static_cast<int32_t>(row_ptr[i]);
+  if ((rc = dev_alloc_t(p, &p->row_ptr, n + 1))) return fail(rc);
+  if ((rc = dev_alloc_t(p, &p->col, std::max<int64_t>(nnz, 1)))) return fail(rc);
+  if ((rc = dev_alloc_t(p, &p->val64, std::max<int64_t>(nnz, 1)))) return fail(rc);
+  if ((rc = cuda_error(cudaMemcpy(p->row_ptr, rp32.data(), 4 * (n + 1), cudaMemcpyHostToDevice), "CSR upload")))
+    return fail(rc);
+  if (nnz > 0) {
+    if ((rc = cuda_error(cudaMemcpy(p->col, col, 4 * nnz, cudaMemcpyHostToDevice), "CSR upload"))) return fail(rc);
+    if ((rc = cuda_error(cudaMemcpy(p->val64, val, 8 * nnz, cudaMemcpyHostToDevice), "CSR upload"))) return fail(rc);
+  }
+  if ((rc = finish_create(p, h))) return fail(rc);
+  cudaStream_t st = p->own_stream;
+  if (precision == NMFA_FP32) {
+    if (p->val_is_int8) {
+      if ((rc = dev_alloc_t(p, &p->val8, std::max<int64_t>(nnz, 1)))) return fail(rc);
+      if (nnz > 0 && (rc = launch_convert_vec(static_cast<int32_t>(nnz), p->val64, p->val8, 3, st))) return fail(rc);
+    } else {
+      if ((rc = dev_alloc_t(p, &p->val32, std::max<int64_t>(nnz, 1)))) return fail(rc);
+      if (nnz > 0 && (rc = launch_convert_vec(static_cast<int32_t>(nnz), p->val64, p->val32, 0, st))) return fail(rc);
+    }
+  } else if (p->val_is_int8) {
+    // FP64 path keeps FP64 values so that its sums match an FP64 evaluation.
+    p->val_is_int8 = false;
+  }
+  if ((rc = cuda_error(cudaStreamSynchronize(st), "create conversions"))) return fail(rc);
+  *out = p;
+  return NMFA_OK;
+}
+
+void nmfa_destroy(nmfa_problem* p) { free_problem(p); }
+
+int nmfa_problem_info(const nmfa_problem* p, int32_t* n, int32_t* precision, int32_t* integer_valued,
+                      int64_t* device_bytes) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (n) *n = p->n;
+  if (precision) *precision = p->precision;
+  if (integer_valued) *integer_valued = p->integer_valued ? 1 : 0;
+  if (device_bytes) *device_bytes = p->device_bytes + static_cast<int64_t>(p->ws.bytes + p->io.bytes + p->sign_scratch.bytes);
+  return NMFA_OK;
+}
+
+int nmfa_profile_enable(nmfa_problem* p, int32_t on) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  p->profiling = on != 0;
+  p->prof_valid = false;
+  return NMFA_OK;
+}
+
+int nmfa_last_kernel_ms(nmfa_problem* p, float* ms) {
+  if (p == nullptr || ms == nullptr) return set_error(NMFA_EINVAL, "NULL argument");
+  if (!p->prof_valid) return set_error(NMFA_EINVAL, "no profiled run");
+  int rc = cuda_error(cudaEventSynchronize(p->prof1), "profile sync");
+  if (rc) return rc;
+  return cuda_error(cudaEventElapsedTime(ms, p->prof0, p->prof1), "profile elapsed");
+}
+
+int nmfa_sync(nmfa_problem* p) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  int rc = cuda_error(cudaEventSynchronize(p->done), "sync");
+  if (rc) return rc;
+  int32_t st = 0;
+  rc = cuda_error(cudaMemcpy(&st, p->status, 4, cudaMemcpyDeviceToHost), "status read");
+  if (rc) return rc;
+  if (st != kStatusOk) {
+    cudaMemset(p->status, 0, 4);
+    return set_error(NMFA_ETIMEOUT, "a bounded device-side wait gave up (status " + std::to_string(st) + ")");
+  }
+  return NMFA_OK;
+}
+
+static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma, double alpha,
+                    int32_t replicas, uint64_t seed, uint32_t stream_id, int32_t noise_sign,
+                    const double* s0_dev, double* s_out_dev, double* phi_out_dev, int8_t* signs_dev,
+                    double* energy_dev, int64_t* energy_i64_dev, cudaStream_t st) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (t_f < 0) return set_error(NMFA_EINVAL, "t_f must be >= 0");
+  if (t_f > 0 && T_dev == nullptr) return set_error(NMFA_EINVAL, "T is NULL");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return set_error(NMFA_EINVAL, "sigma must be >= 0");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return set_error(NMFA_EINVAL, "alpha must be in (0, 1]");
+  if (replicas < 1) return set_error(NMFA_EINVAL, "replicas must be >= 1");
+  if (noise_sign < -1 || noise_sign > 1) return set_error(NMFA_EINVAL, "noise_sign must be -1, 0 or 1");
+  if (energy_i64_dev != nullptr && !p->integer_valued)
+    return set_error(NMFA_EINVAL, "integer energies requested for a real-valued problem");
+  if (static_cast<int64_t>(replicas) * p->n > (1ll << 40)) return set_error(NMFA_EINVAL, "replicas * n too large");
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(p->device), "cudaSetDevice"))) return rc;
+  // Runs on one handle share its scratch: order this run after the previous one.
+  if ((rc = cuda_error(cudaStreamWaitEvent(st, p->done, 0), "stream wait"))) return rc;
+  if (signs_dev == nullptr) {
+    if ((rc = ensure_buf(p->sign_scratch, static_cast<size_t>(replicas) * p->n))) return rc;
+    signs_dev = static_cast<int8_t*>(p->sign_scratch.p);
+  }
+  RunParams rp{};
+  rp.T = T_dev;
+  rp.t_f = t_f;
+  rp.sigma = sigma;
+  rp.alpha = alpha;
+  rp.replicas = replicas;
+  rp.seed = seed;
+  rp.stream_id = stream_id;
+  rp.noise_sign = noise_sign;
+  rp.s0 = s0_dev;
+  rp.s_out = s_out_dev;
+  rp.phi_out = phi_out_dev;
+  rp.signs = signs_dev;
+  if (p->profiling && (rc = cuda_error(cudaEventRecord(p->prof0, st), "profile event"))) return rc;
+  switch (p->precision) {
+    case NMFA_FP64:
+    case NMFA_FP32: {
+      const bool f64 = p->precision == NMFA_FP64;
+      if (p->csr) {
+        CsrProblem pb{};
+        pb.n = p->n;
+        pb.nnz = p->nnz;
+        pb.row_ptr = p->row_ptr;
+        pb.col = p->col;
+        pb.val_int8 = !f64 && p->val_is_int8;
+        pb.val = f64 ? static_cast<const void*>(p->val64)
+                     : (pb.val_int8 ? static_cast<const void*>(p->val8) : static_cast<const void*>(p->val32));
+        pb.h = f64 ? static_cast<const void*>(p->h64) : static_cast<const void*>(p->h32);
+        pb.d = p->d64;
+        pb.inv_d32 = p->inv_d32;
+        rc = launch_csr(f64, pb, rp, st, p->replicas_per_cta);
+      } else {
+        DenseSimtProblem pb{};
+        pb.n = p->n;
+        pb.J = f64 ? static_cast<const void*>(p->J64) : static_cast<const void*>(p->J32);
+        pb.h = f64 ? static_cast<const void*>(p->h64) : static_cast<const void*>(p->h32);
+        pb.d = p->d64;
+        pb.inv_d32 = p->inv_d32;
+        rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
+      }
+      break;
+    }
+    default: {
+      TcProblem pb{};
+      pb.n = p->n;
+      pb.n_pad = p->n_pad;
+      pb.Jq = p->Jq;
+      pb.fp8 = p->precision == NMFA_BF16_FP8J;
+      pb.inv_d32 = p->inv_d32;
+      pb.h32 = p->h32;
+      int64_t bytes = 0;
+      if ((rc = tc_workspace_bytes(pb, replicas, &bytes))) return rc;
+      if ((rc = ensure_buf(p->ws, static_cast<size_t>(bytes)))) return rc;
+      TcWorkspace ws{};
+      ws.S16 = p->ws.p;
+      ws.bytes = bytes;
+      ws.status = p->status;
+      rc = launch_tc(pb, rp, ws, st);
+      break;
+    }
+  }
+  if (rc) return rc;
+  if (p->profiling) {
+    if ((rc = cuda_error(cudaEventRecord(p->prof1, st), "profile event"))) return rc;
+    p->prof_valid = true;
+  }
+  if (energy_dev != nullptr || energy_i64_dev != nullptr) {
+    EnergyProblem ep{};
+    ep.n = p->n;
+    ep.J8 = p->J8;
+    ep.J64 = p->csr ? nullptr : p->J64;
+    ep.row_ptr = p->csr ? p->row_ptr : nullptr;
+    ep.col = p->col;
+    ep.val64 = p->val64;
+    ep.h = p->h64;
+    ep.integer_valued = p->integer_valued;
+    if ((rc = launch_energy(ep, signs_dev, replicas, energy_dev, energy_i64_dev, st))) return rc;
+  }
+  return cuda_error(cudaEventRecord(p->done, st), "event record");
+}
+
+int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma, double alpha,
+                    int32_t replicas, uint64_t seed, uint32_t stream_id, int8_t* signs_dev,
+                    double* energy_dev, int64_t* energy_i64_dev, void* cuda_stream) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  std::lock_guard<std::mutex> g(p->mu);
+  return run_impl(p, T_dev, t_f, sigma, alpha, replicas, seed, stream_id, 1, nullptr, nullptr, nullptr,
+                  signs_dev, energy_dev, energy_i64_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int nmfa_debug_run(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma, double alpha,
+                   int32_t replicas, uint64_t seed, uint32_t stream_id, int32_t noise_sign,
+                   const double* s0_dev, double* s_out_dev, double* phi_out_dev, int8_t* signs_dev,
+                   double* energy_dev, int64_t* energy_i64_dev, void* cuda_stream) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  std::lock_guard<std::mutex> g(p->mu);
+  return run_impl(p, T_dev, t_f, sigma, alpha, replicas, seed, stream_id, noise_sign, s0_dev, s_out_dev,
+                  phi_out_dev, signs_dev, energy_dev, energy_i64_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int nmfa_run(nmfa_problem* p, const double* T, int32_t t_f, double sigma, double alpha, int32_t replicas,
+             uint64_t seed, uint32_t stream_id, int8_t* signs_out, double* energy_out, int64_t* energy_i64_out) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (t_f < 0 || replicas < 1) return set_error(NMFA_EINVAL, "t_f must be >= 0 and replicas >= 1");
+  if (t_f > 0 && T == nullptr) return set_error(NMFA_EINVAL, "T is NULL");
+  for (int32_t t = 0; t < t_f; ++t)
+    if (!(T[t] > 0.0) || !std::isfinite(T[t])) return set_error(NMFA_EINVAL, "every T_t must be finite and > 0");
+  if (energy_i64_out != nullptr && !p->integer_valued)
+    return set_error(NMFA_EINVAL, "integer energies requested for a real-valued problem");
+  std::lock_guard<std::mutex> g(p->mu);
+  const size_t signs_b = static_cast<size_t>(replicas) * p->n;
+  const size_t off_T = 0;
+  const size_t off_E = (sizeof(double) * std::max(t_f, 1) + 255) / 256 * 256;
+  const size_t off_Ei = off_E + (sizeof(double) * replicas + 255) / 256 * 256;
+  const size_t off_S = off_Ei + (sizeof(int64_t) * replicas + 255) / 256 * 256;
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(p->device), "cudaSetDevice"))) return rc;
+  if ((rc = cuda_error(cudaEventSynchronize(p->done), "sync"))) return rc;
+  if ((rc = ensure_buf(p->io, off_S + signs_b))) return rc;
+  char* base = static_cast<char*>(p->io.p);
+  double* T_dev = reinterpret_cast<double*>(base + off_T);
+  double* E_dev = reinterpret_cast<double*>(base + off_E);
+  int64_t* Ei_dev = reinterpret_cast<int64_t*>(base + off_Ei);
+  int8_t* S_dev = reinterpret_cast<int8_t*>(base + off_S);
+  cudaStream_t st = p->own_stream;
+  if (t_f > 0 && (rc = cuda_error(cudaMemcpyAsync(T_dev, T, sizeof(double) * t_f, cudaMemcpyHostToDevice, st), "T upload")))
+    return rc;
+  rc = run_impl(p, T_dev, t_f, sigma, alpha, replicas, seed, stream_id, 1, nullptr, nullptr, nullptr, S_dev,
+                energy_out ? E_dev : nullptr, energy_i64_out ? Ei_dev : nullptr, st);
+  if (rc) return rc;
+  if (signs_out && (rc = cuda_error(cudaMemcpyAsync(signs_out, S_dev, signs_b, cudaMemcpyDeviceToHost, st), "signs download")))
+    return rc;
+  if (energy_out && (rc = cuda_error(cudaMemcpyAsync(energy_out, E_dev, sizeof(double) * replicas, cudaMemcpyDeviceToHost, st), "energy download")))
+    return rc;
+  if (energy_i64_out && (rc = cuda_error(cudaMemcpyAsync(energy_i64_out, Ei_dev, sizeof(int64_t) * replicas, cudaMemcpyDeviceToHost, st), "energy download")))
+    return rc;
+  if ((rc = cuda_error(cudaStreamSynchronize(st), "run"))) return rc;
+  int32_t status = 0;
+  if ((rc = cuda_error(cudaMemcpy(&status, p->status, 4, cudaMemcpyDeviceToHost), "status read"))) return rc;
+  if (status != kStatusOk) {
+    cudaMemset(p->status, 0, 4);
+    return set_error(NMFA_ETIMEOUT, "a bounded device-side wait gave up");
+  }
+  return NMFA_OK;
+}
+
+// Tuning hook for the CUDA-core paths (replicas per CTA: 0 = automatic, else 1/2/4/8).
+int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (rc != 0 && rc != 1 && rc != 2 && rc != 4 && rc != 8) return set_error(NMFA_EINVAL, "rc must be 0, 1, 2, 4 or 8");
+  p->replicas_per_cta = rc;
+  return NMFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// nmfa_internal.h -- structures shared between the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "../../include/nmfa.h"
+
+namespace nmfa {
+
+// Process-wide count of kernel launches made by the library.
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Thread-local error message; returns `code` for convenience.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+// Device-side status word written by kernels with bounded waits.
+enum DeviceStatus : int32_t { kStatusOk = 0, kStatusTimeout = 1 };
+
+// One run's parameters as the kernels see them.
+struct RunParams {
+  const double* T;        // device, t_f temperatures
+  int32_t t_f;
+  double sigma;
+  double alpha;
+  int32_t replicas;
+  uint64_t seed;
+  uint32_t stream_id;
+  int32_t noise_sign;
+  const double* s0;       // device R*n or nullptr
+  double* s_out;          // device R*n or nullptr
+  double* phi_out;        // device R*n or nullptr
+  int8_t* signs;          // device R*n (always present: the library supplies scratch)
+};
+
+// ---- CUDA-core dense path (FP32 / FP64) -----------------------------------
+struct DenseSimtProblem {
+  int32_t n;
+  const void* J;          // float or double, row-major n*n (symmetric)
+  const void* h;          // float or double, n (zeros when h = 0)
+  const double* d;        // FP64 row norms
+  const float* inv_d32;   // 1/d_i in binary32 (0 where d_i = 0)
+};
+int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
+                      cudaStream_t st, int replicas_per_cta);
+
+// ---- CUDA-core CSR path (FP32 / FP64) ---------------------------------------
+struct CsrProblem {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* row_ptr; // n+1
+  const int32_t* col;     // nnz
+  const void* val;        // float/double nnz, or int8 when val_int8
+  bool val_int8;
+  const void* h;
+  const double* d;
+  const float* inv_d32;
+};
+int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,
+               int replicas_per_cta);
+
+// ---- Eq. (1) energies from signs --------------------------------------------
+struct EnergyProblem {
+  int32_t n;
+  const int8_t* J8;       // int8 copy (integer problems with |J| <= 127) or nullptr
+  const double* J64;      // FP64 copy (used when J8 is null)
+  const int32_t* row_ptr; // CSR form (used when non-null)
+  const int32_t* col;
+  const double* val64;
+  const double* h;        // FP64 fields or nullptr
+  bool integer_valued;
+};
+int launch_energy(const EnergyProblem& ep, const int8_t* signs, int32_t replicas,
+                  double* energy, int64_t* energy_i64, cudaStream_t st);
+
+// ---- preparation kernels ------------------------------------------------------
+int launch_row_norms_dense(int32_t n, const double* J64, const double* h, double* d,
+                           float* inv_d32, cudaStream_t st);
+int launch_row_norms_csr(int32_t n, const int32_t* row_ptr, const double* val64,
+                         const double* h, double* d, float* inv_d32, cudaStream_t st);
+// dst[i*ld + j] = convert(J64[i*n + j]) for i,j < n, zero in the padding up to
+// rows x ld.  kind: 0 = float, 1 = bf16, 2 = e4m3, 3 = int8.
+int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int64_t rows,
+                         int64_t ld, cudaStream_t st);
+int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st);
+
+// ---- tcgen05 tensor path ------------------------------------------------------
+struct TcProblem {
+  int32_t n;
+  int32_t n_pad;          // spins padded to a multiple of 128 (rows and K)
+  const void* Jq;         // BF16 [n_pad][n_pad] or E4M3 [n_pad][n_pad]
+  bool fp8;
+  const float* inv_d32;   // n_pad, 0 in padding
+  const float* h32;       // h_i in binary32, n_pad (0 in padding)
+};
+struct TcWorkspace {
+  void* S16;              // bf16 [2][r_pad][n_pad]
+  uint32_t* flags;        // [row blocks][replica blocks]
+  int32_t* status;
+  int64_t bytes;
+};
+int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes);
+int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,
+              cudaStream_t st);
+
+}  // namespace nmfa

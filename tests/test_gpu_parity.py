@@ -1,0 +1,270 @@
+"""Parity of the CUDA paths (through the C ABI) with the FP64 oracle.
+
+Tolerances (Algorithm 1 line 6, from identical state; "relative" is measured
+against the forward-error scale (|h_i| + sum_j |J_ij s_j|)/d_i + sigma |z|):
+  FP64 <= 1e-12, FP32 <= 1e-5, BF16 (tensor path) <= 4e-3.
+sigma = 0 FP64 trajectories agree to <= 1e-9 over t_f = 1000 steps; energies of
+integer problems are bit-exact in int64; success probabilities of full runs fall in
+the oracle's 95% Wilson interval over >= 1000 paired runs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_08422_gb300 import instances as inst
+from tests.helpers import Gpu, phi_scale, wilson
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 4e-3}
+DENSE = ["fp64", "fp32", "bf16"]
+
+
+def _rand_state(R, n, seed):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(R, n))
+
+
+# ---------------------------------------------------------------- single step
+@pytest.mark.parametrize("prec", DENSE)
+@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64)])
+def test_single_step_phi(prec, n, R):
+    J = inst.sk(n, 100 + n) if n > 1 else np.zeros((1, 1))
+    h = inst.random_fields(n, 0.5, 7) if prec != "bf16" else None
+    sigma, alpha, seed, stream = 0.15, 0.15, 1234, 3
+    s0 = _rand_state(R, n, n)
+    T = [0.8]
+    ref = oracle.run(J, T, sigma, alpha, R, seed=seed, stream=stream, h=h, s0=s0, want_phi=True,
+                     want_state=True)
+    g = Gpu(J, h=h, precision=prec)
+    out = g.run(T, sigma, alpha, R, seed=seed, stream_id=stream, s0=s0, want_phi=True, want_state=True)
+    scale = phi_scale(J, s0, h, sigma, seed, stream)
+    err = np.abs(out["phi"] - ref["phi"]) / np.maximum(scale, 1e-300)
+    assert err.max() <= TOL[prec], (prec, float(err.max()))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", DENSE)
+def test_single_step_full_size_sampled(prec):
+    # SK N = 2000 with 1024 replicas in the launch configuration of the benchmark;
+    # the oracle recomputes sampled replica slices from every replica block.
+    n, R = 2000, 1024
+    if prec == "fp64":
+        R = 256
+    J = inst.sk(n, 0)
+    sigma, alpha, seed, stream = 0.15, 0.15, 0, 0
+    s0 = _rand_state(R, n, 5)
+    g = Gpu(J, precision=prec)
+    out = g.run([1.3], sigma, alpha, R, seed=seed, stream_id=stream, s0=s0, want_phi=True)
+    for r0 in (0, 100, R - 13):
+        sl = slice(r0, r0 + 4)
+        ref = oracle.run(J, [1.3], sigma, alpha, 4, seed=seed, stream=stream, s0=s0[sl], want_phi=True,
+                         r_first=r0, nthreads=0)
+        scale = phi_scale(J, s0[sl], None, sigma, seed, stream, r_first=r0)
+        err = np.abs(out["phi"][sl] - ref["phi"]) / scale
+        assert err.max() <= TOL[prec], (prec, r0, float(err.max()))
+    g.close()
+
+
+def test_noise_stream_identical_fp64():
+    # h = 0, s = 0: Phi = sigma z exactly, so the GPU's draws are visible; the
+    # Philox words and the Box-Muller pairing must be those of the oracle.
+    n, R = 37, 11
+    J = inst.sk(n, 3)
+    g = Gpu(J, precision="fp64")
+    for seed, stream in [(0, 0), (0xDEADBEEF12345678, 7)]:
+        out = g.run([1.0], 1.0, 0.15, R, seed=seed, stream_id=stream, want_phi=True)
+        z = np.array([[oracle.gauss(seed, stream, r, 0, i) for i in range(n)] for r in range(R)])
+        np.testing.assert_allclose(out["phi"], z, rtol=1e-13, atol=1e-13)
+    g.close()
+
+
+# ---------------------------------------------------------------- trajectories
+def test_sigma0_fp64_trajectory():
+    n, R, t_f = 100, 8, 1000
+    J = inst.sk(n, 1)
+    h = inst.random_fields(n, 0.3, 2)
+    T = inst.schedule(t_f)
+    ref = oracle.run(J, T, 0.0, 0.15, R, h=h, want_state=True)
+    g = Gpu(J, h=h, precision="fp64")
+    out = g.run(T, 0.0, 0.15, R, want_state=True)
+    assert np.abs(out["state"] - ref["state"]).max() <= 1e-9
+    np.testing.assert_array_equal(out["signs"], ref["signs"])
+    g.close()
+
+
+def test_sigma0_fp64_trajectory_from_state():
+    n, R, t_f = 160, 6, 400
+    J = inst.gnp_maxcut(n, 0.5, 4)
+    s0 = _rand_state(R, n, 9) * 0.1
+    T = inst.schedule(t_f)
+    ref = oracle.run(J, T, 0.0, 0.15, R, s0=s0, want_state=True)
+    g = Gpu(J, precision="fp64")
+    out = g.run(T, 0.0, 0.15, R, s0=s0, want_state=True)
+    assert np.abs(out["state"] - ref["state"]).max() <= 1e-9
+    g.close()
+
+
+# ---------------------------------------------------------------- energies
+@pytest.mark.parametrize("prec", DENSE)
+def test_integer_energies_bit_exact(prec):
+    n, R = 300, 64
+    for J in (inst.sk(n, 11), inst.gnp_maxcut(n, 0.5, 12), inst.moebius(n)):
+        g = Gpu(J, precision=prec)
+        out = g.run(inst.schedule(50), 0.15, 0.15, R, seed=5)
+        ref = np.array([oracle.energy_i64(J, out["signs"][r]) for r in range(R)], dtype=np.int64)
+        np.testing.assert_array_equal(out["energy_i64"], ref)
+        np.testing.assert_array_equal(out["energy"], ref.astype(np.float64))
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_real_valued_energies_fp64(prec):
+    n, R = 120, 16
+    J = inst.random_real_couplings(n, 13, density=0.7)
+    h = inst.random_fields(n, 0.7, 14)
+    g = Gpu(J, h=h, precision=prec)
+    out = g.run(inst.schedule(40), 0.15, 0.15, R, seed=6)
+    assert out["energy_i64"] is None
+    mag = np.abs(np.triu(J, 1)).sum() + np.abs(h).sum()
+    for r in range(R):
+        assert abs(out["energy"][r] - oracle.energy(J, out["signs"][r], h)) <= 1e-12 * mag
+    g.close()
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("prec", DENSE)
+def test_noise_negation_symmetry_gpu(prec):
+    n, R = 200, 32
+    J = inst.sk(n, 15)
+    T = inst.schedule(100)
+    g = Gpu(J, precision=prec)
+    a = g.run(T, 0.15, 0.15, R, seed=8, want_state=True)
+    b = g.run(T, 0.15, 0.15, R, seed=8, noise_sign=-1, want_state=True)
+    np.testing.assert_array_equal(a["state"], -b["state"])
+    np.testing.assert_array_equal(a["energy_i64"], b["energy_i64"])
+    g.close()
+
+
+@pytest.mark.parametrize("prec", DENSE)
+def test_zero_state_and_state_bound(prec):
+    n, R = 130, 20
+    J = inst.sk(n, 16)
+    g = Gpu(J, precision=prec)
+    out = g.run(inst.schedule(30), 0.0, 0.15, R, want_state=True)
+    assert np.all(out["state"] == 0.0) and np.all(out["signs"] == 1)
+    assert np.all(out["energy_i64"] == int(np.triu(J, 1).sum()))
+    for tf in (0, 1, 7):
+        st = g.run(inst.schedule(40)[:tf], 0.15, 0.15, R, seed=2, want_state=True)["state"]
+        assert np.all(np.abs(st) <= 1.0 - (1.0 - 0.15) ** tf + 1e-6)
+    g.close()
+
+
+# ---------------------------------------------------------------- sparse path
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_csr_single_step(prec):
+    for J in (inst.moebius(400), inst.regular3(300, 3)):
+        n, R = J.shape[0], 48
+        csr = inst.to_csr(J)
+        h = inst.random_fields(n, 0.4, 17)
+        s0 = _rand_state(R, n, 18)
+        ref = oracle.run(None, [0.9], 0.15, 0.15, R, seed=4, h=h, s0=s0, want_phi=True, csr=csr)
+        g = Gpu(None, h=h, precision=prec, csr=csr, n=n)
+        out = g.run([0.9], 0.15, 0.15, R, seed=4, s0=s0, want_phi=True)
+        scale = phi_scale(J, s0, h, 0.15, 4, 0)
+        err = np.abs(out["phi"] - ref["phi"]) / scale
+        assert err.max() <= TOL[prec]
+        g.close()
+
+
+def test_csr_sigma0_fp64_trajectory_and_energy():
+    J = inst.moebius(100)
+    n, R = 100, 8
+    csr = inst.to_csr(J)
+    h = inst.random_fields(n, 0.3, 19)
+    T = inst.schedule(1000)
+    ref = oracle.run(None, T, 0.0, 0.15, R, h=h, want_state=True, csr=csr)
+    g = Gpu(None, h=h, precision="fp64", csr=csr, n=n)
+    out = g.run(T, 0.0, 0.15, R, want_state=True)
+    assert np.abs(out["state"] - ref["state"]).max() <= 1e-9
+    g.close()
+    g = Gpu(None, precision="fp32", csr=csr, n=n)
+    out = g.run(T, 0.15, 0.15, 64, seed=3)
+    ref_e = np.array([oracle.energy_i64(J, out["signs"][r]) for r in range(64)])
+    np.testing.assert_array_equal(out["energy_i64"], ref_e)
+    g.close()
+
+
+# ---------------------------------------------------------------- full runs
+def _success_counts(J, T, runs, prec, csr=None, target=None):
+    out = Gpu(J if csr is None else None, precision=prec, csr=csr, n=J.shape[0]).run(T, 0.15, 0.15, runs, seed=21)
+    return int(np.sum(out["energy_i64"] <= target))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64", "csr_fp32"])
+def test_success_probability_moebius16(prec):
+    # Fig. 3's 16-spin Moebius ladder with the schedule compressed to 100 steps;
+    # ground energy -20 (closed form).  GPU and oracle runs are paired by stream.
+    J = inst.moebius(16)
+    T = inst.schedule(100)
+    runs = 1000
+    ref = oracle.run(J, T, 0.15, 0.15, runs, seed=21)
+    k_ref = int(np.sum(ref["energy_i64"] <= -20))
+    lo, hi = wilson(k_ref, runs)
+    if prec == "csr_fp32":
+        k = _success_counts(J, T, runs, "fp32", csr=inst.to_csr(J), target=-20)
+    else:
+        k = _success_counts(J, T, runs, prec, target=-20)
+    assert lo <= k / runs <= hi, (prec, k / runs, k_ref / runs, lo, hi)
+
+
+def test_success_probability_sk20_tensor():
+    J = inst.sk(20, 31)
+    e0, _, _ = oracle.brute_force(J)
+    T = inst.schedule(200)
+    runs = 1024
+    ref = oracle.run(J, T, 0.15, 0.15, runs, seed=21)
+    lo, hi = wilson(int(np.sum(ref["energy_i64"] <= e0)), runs)
+    k = _success_counts(J, T, runs, "bf16", target=e0)
+    assert lo <= k / runs <= hi
+
+
+def test_host_api_matches_device_api():
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(150, 40)
+    T = inst.schedule(200)
+    g = Gpu(J, precision="bf16")
+    dev = g.run(T, 0.15, 0.15, 96, seed=9, stream_id=2)
+    signs, e, ei = nmfa.nmfa_run(g.p.handle, 150, T, 0.15, 0.15, 96, 9, 2, True)
+    np.testing.assert_array_equal(signs, dev["signs"])
+    np.testing.assert_array_equal(ei, dev["energy_i64"])
+    g.close()
+
+
+def test_tensor_two_waves():
+    # More replica blocks than fit co-resident: the launch is split into waves of
+    # whole replica blocks; every replica still matches the oracle's single step.
+    n, R = 2000, 2560
+    J = inst.sk(n, 2)
+    s0 = _rand_state(R, n, 3)
+    g = Gpu(J, precision="bf16")
+    out = g.run([1.1], 0.15, 0.15, R, seed=1, s0=s0, want_phi=True)
+    r0 = R - 4
+    ref = oracle.run(J, [1.1], 0.15, 0.15, 4, seed=1, s0=s0[r0:], want_phi=True, r_first=r0)
+    scale = phi_scale(J, s0[r0:], None, 0.15, 1, 0, r_first=r0)
+    assert (np.abs(out["phi"][r0:] - ref["phi"]) / scale).max() <= 4e-3
+    g.close()
+
+
+def test_full_c2_run_readout_and_energy():
+    # The benchmark configuration end to end: SK N = 2000, 1024 replicas, t_f = 1000.
+    n, R = 2000, 1024
+    J = inst.sk(n, 0)
+    g = Gpu(J, precision="bf16")
+    out = g.run(inst.schedule(1000), 0.15, 0.15, R, seed=0, want_state=True)
+    assert np.all(np.abs(out["state"]) <= 1.0)
+    np.testing.assert_array_equal(out["signs"], np.where(out["state"] >= 0, 1, -1))
+    for r in (0, 511, 1023):
+        assert out["energy_i64"][r] == oracle.energy_i64(J, out["signs"][r])
+    dens = out["energy_i64"].mean() / n ** 1.5
+    assert -0.80 < dens < -0.60, dens
+    g.close()
