@@ -130,6 +130,35 @@ int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
                     int8_t* signs_dev, double* energy_dev, int64_t* energy_i64_dev,
                     void* cuda_stream);
 
+/*
+ * nmfa_run_device_noalloc -- nmfa_run_device for an NMFA_BF16 problem that allocates
+ * nothing.  The paper has no counterpart; this exists for callers that cannot
+ * allocate device memory while they run: code inside a CUDA stream capture (an
+ * allocation there is not part of the graph and may synchronise the device), a
+ * framework whose memory pool owns all device memory, or a serving loop that must
+ * not pay for or serialise on cudaMalloc.  The handle itself was allocated by
+ * nmfa_create beforehand; this call only reuses it.
+ *
+ * The tensor kernel's scratch (two BF16 copies of the state and one epoch flag per
+ * tile) comes from a static device array of 16 MiB that every GPU loading this
+ * library holds until the process exits.  The scratch needed is
+ * 4 * ceil(R/BN)*BN * ceil(n/128)*128 bytes plus the flags (BN = 64 for R <= 64,
+ * else 128); larger sizes return NMFA_EINVAL with nothing launched (e.g. n = 2000
+ * takes up to R = 1920).  The flags are cleared on the stream before each launch;
+ * the state buffers are fully written by the kernel before they are read.
+ *   signs_dev  R*n int8, required (no scratch is made for signs)
+ *   energy_dev, energy_i64_dev  as in nmfa_run_device (may be NULL)
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * uses the same array, so calls whose kernels overlap on the GPU (different
+ * streams, different handles) race and give wrong results: serialise them.
+ * Returns NMFA_EUNSUPPORTED for other precisions.
+ */
+int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f,
+                            double sigma, double alpha, int32_t replicas, uint64_t seed,
+                            uint32_t stream_id, int8_t* signs_dev, double* energy_dev,
+                            int64_t* energy_i64_dev, void* cuda_stream);
+
 /* Waits for the handle's last run and returns its device-side status
  * (NMFA_OK or NMFA_ETIMEOUT) or a CUDA error. */
 int nmfa_sync(nmfa_problem* p);

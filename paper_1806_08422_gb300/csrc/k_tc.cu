@@ -474,4 +474,56 @@ int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, c
   return pick_bn(rp.replicas) == 64 ? launch_tc_bn<64>(pb, rp, ws, st) : launch_tc_bn<128>(pb, rp, ws, st);
 }
 
+// ----------------------------------------------------------------------------
+// Scratch without allocation, for nmfa_run_device_noalloc.
+//
+// The tensor path's scratch (the two BF16 state buffers and the per-tile epoch
+// flags) normally lives in memory the problem handle allocates on demand.  Callers
+// that must not allocate device memory get it from this file-scope array instead.
+// It is created when the GPU loads this library's device code and stays there
+// until the process exits, on every GPU that loads the library.  Host code cannot
+// use the symbol itself as a device address, so its address is looked up once per
+// device (with that device current) and cached.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+}  // namespace
+
+int tc_static_scratch(void** ptr, size_t* bytes) {
+  static std::mutex mu;
+  static void* addr[128] = {};
+  int dev = 0;
+  int rc = cuda_error(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= 128) return set_error(NMFA_EUNSUPPORTED, "device ordinal out of range for static scratch");
+  std::lock_guard<std::mutex> g(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    rc = cuda_error(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress(static scratch)");
+    if (rc) return rc;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  *bytes = kStaticScratchBytes;
+  return NMFA_OK;
+}
+
+int launch_tc_static_scratch(const TcProblem& pb, const RunParams& rp, int32_t* status, cudaStream_t st) {
+  int64_t need = 0;
+  int rc = tc_workspace_bytes(pb, rp.replicas, &need);
+  if (rc) return rc;
+  if (need > static_cast<int64_t>(kStaticScratchBytes))
+    return set_error(NMFA_EINVAL, "nmfa_run_device_noalloc: this size needs " + std::to_string(need) +
+                                      " bytes of scratch, more than the 16 MiB static buffer");
+  void* p = nullptr;
+  size_t bytes = 0;
+  if ((rc = tc_static_scratch(&p, &bytes))) return rc;
+  TcWorkspace ws{};
+  ws.S16 = p;
+  ws.status = status;
+  ws.bytes = need;
+  return launch_tc(pb, rp, ws, st);  // clears the epoch flags before the kernel runs
+}
+
 }  // namespace nmfa

@@ -588,6 +588,56 @@ int nmfa_run(nmfa_problem* p, const double* T, int32_t t_f, double sigma, double
   return NMFA_OK;
 }
 
+// The allocation-free variant of nmfa_run_device for the tensor path: the kernel's
+// scratch comes from a static device array (see launch_tc_static_scratch), signs must
+// be supplied by the caller, and nothing on this path allocates device or host memory.
+int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma, double alpha,
+                            int32_t replicas, uint64_t seed, uint32_t stream_id, int8_t* signs_dev,
+                            double* energy_dev, int64_t* energy_i64_dev, void* cuda_stream) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (p->precision != NMFA_BF16) return set_error(NMFA_EUNSUPPORTED, "nmfa_run_device_noalloc takes NMFA_BF16 problems");
+  if (signs_dev == nullptr) return set_error(NMFA_EINVAL, "nmfa_run_device_noalloc needs a signs buffer");
+  if (t_f < 0 || (t_f > 0 && T_dev == nullptr)) return set_error(NMFA_EINVAL, "bad t_f or T");
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) return set_error(NMFA_EINVAL, "sigma must be >= 0");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return set_error(NMFA_EINVAL, "alpha must be in (0, 1]");
+  if (replicas < 1) return set_error(NMFA_EINVAL, "replicas must be >= 1");
+  if (energy_i64_dev != nullptr && !p->integer_valued)
+    return set_error(NMFA_EINVAL, "integer energies requested for a real-valued problem");
+  std::lock_guard<std::mutex> g(p->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(p->device), "cudaSetDevice"))) return rc;
+  if ((rc = cuda_error(cudaStreamWaitEvent(st, p->done, 0), "stream wait"))) return rc;
+  RunParams rp{};
+  rp.T = T_dev;
+  rp.t_f = t_f;
+  rp.sigma = sigma;
+  rp.alpha = alpha;
+  rp.replicas = replicas;
+  rp.seed = seed;
+  rp.stream_id = stream_id;
+  rp.noise_sign = 1;
+  rp.signs = signs_dev;
+  TcProblem pb{};
+  pb.n = p->n;
+  pb.n_pad = p->n_pad;
+  pb.Jq = p->Jq;
+  pb.fp8 = false;
+  pb.inv_d32 = p->inv_d32;
+  pb.h32 = p->h32;
+  if ((rc = launch_tc_static_scratch(pb, rp, p->status, st))) return rc;
+  if (energy_dev != nullptr || energy_i64_dev != nullptr) {
+    EnergyProblem ep{};
+    ep.n = p->n;
+    ep.J8 = p->J8;
+    ep.J64 = p->J64;
+    ep.h = p->h64;
+    ep.integer_valued = p->integer_valued;
+    if ((rc = launch_energy(ep, signs_dev, replicas, energy_dev, energy_i64_dev, st))) return rc;
+  }
+  return cuda_error(cudaEventRecord(p->done, st), "event record");
+}
+
 // Tuning hook for the CUDA-core paths (replicas per CTA: 0 = automatic, else 1/2/4/8).
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
   if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");

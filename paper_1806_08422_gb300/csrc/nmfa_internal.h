@@ -106,5 +106,8 @@ struct TcWorkspace {
 int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes);
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,
               cudaStream_t st);
+// Same launch with the scratch taken from a fixed-size static device array.
+int launch_tc_static_scratch(const TcProblem& pb, const RunParams& rp, int32_t* status,
+                             cudaStream_t st);
 
 }  // namespace nmfa

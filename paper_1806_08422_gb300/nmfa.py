@@ -39,6 +39,7 @@ SIGNATURES = {
     "nmfa_destroy": (None, [_P]),
     "nmfa_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _P, _P, _P]),
     "nmfa_run_device": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _P, _P, _P, _P]),
+    "nmfa_run_device_noalloc": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _P, _P, _P, _P]),
     "nmfa_sync": (ctypes.c_int, [_P]),
     "nmfa_debug_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _i32, _P, _P, _P, _P, _P,
                                       _P, _P]),
@@ -137,6 +138,14 @@ def nmfa_run_device(handle, T_dev, sigma, alpha, replicas, seed=0, stream_id=0, 
     _check(load().nmfa_run_device(handle, _t_ptr(T_dev), int(T_dev.numel()), float(sigma), float(alpha),
                                   int(replicas), int(seed), int(stream_id), _t_ptr(signs), _t_ptr(energy),
                                   _t_ptr(energy_i64), _stream_ptr(stream)))
+
+
+def nmfa_run_device_noalloc(handle, T_dev, sigma, alpha, replicas, seed=0, stream_id=0, signs=None, energy=None,
+                            energy_i64=None, stream=None):
+    """nmfa_run_device for a BF16 problem without any allocation (static scratch)."""
+    _check(load().nmfa_run_device_noalloc(handle, _t_ptr(T_dev), int(T_dev.numel()), float(sigma), float(alpha),
+                                          int(replicas), int(seed), int(stream_id), _t_ptr(signs), _t_ptr(energy),
+                                          _t_ptr(energy_i64), _stream_ptr(stream)))
 
 
 def nmfa_debug_run(handle, T_dev, sigma, alpha, replicas, seed=0, stream_id=0, noise_sign=1, s0=None,
