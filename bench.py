@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--tf", type=int, default=T_F, help="steps per run (profiling of a shorter run)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -183,14 +184,15 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     J = inst.sk(N_SPINS, 0)
-    T = inst.schedule(T_F)
+    T = inst.schedule(T_F)[:args.tf]
     prob = nmfa.Problem(J, precision=args.precision)
     Td = torch.as_tensor(T, device=dev)
     signs = torch.empty((REPLICAS, N_SPINS), dtype=torch.int8, device=dev)
     energy = torch.empty(REPLICAS, dtype=torch.float64, device=dev)
     energy_i64 = torch.empty(REPLICAS, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream_id = rank  # each rank anneals its own independent replicas
+    from paper_1806_08422_gb300 import multi
+    stream_id = multi.rank_stream(rank)  # each rank anneals its own independent replicas
 
     def one_step():
         prob.run_device(Td, SIGMA, ALPHA, REPLICAS, seed=0, stream_id=stream_id, signs=signs, energy=energy,
@@ -227,10 +229,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units_per_step = REPLICAS * N_SPINS * T_F
+        total_ms = multi.max_over_ranks(total_ms, device=dev)
+    units_per_step = REPLICAS * N_SPINS * args.tf
     value = units_per_step * ws * args.steps / (total_ms / 1e3)
 
     # end to end through the host-buffer C call (T upload, signs + energies download)
@@ -242,15 +242,13 @@ def main():
         nmfa.nmfa_run(prob.handle, N_SPINS, T, SIGMA, ALPHA, REPLICAS, 0, stream_id, True)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": units_per_step * ws / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": T_F * 8,
+        e2e_s = multi.max_over_ranks(e2e_s, device=dev)
+    e2e = {"value": units_per_step * ws / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": args.tf * 8,
            "d2h_bytes_per_step": REPLICAS * N_SPINS + REPLICAS * 8 * 2}
 
     peaks, peak_kind = _peaks()
     kern_ms = statistics.mean(kernel_ms)
-    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * T_F
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * args.tf
     if args.precision == "bf16":
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         achieved = flops / (kern_ms / 1e3) / 1e12
@@ -288,7 +286,7 @@ def main():
                                        "default 3-segment schedule; %s" % (
                                            "BF16 J/S, FP32 accumulation on tcgen05" if args.precision == "bf16"
                                            else args.precision + " CUDA-core path"),
-                           "n": N_SPINS, "replicas_per_gpu": REPLICAS, "t_f": T_F,
+                           "n": N_SPINS, "replicas_per_gpu": REPLICAS, "t_f": args.tf,
                            "l2": "flushed between timed steps (256 MB write, outside the step events)",
                            "parallelism": "replicas" if ws == 1 else "replicas x%d ranks" % ws},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

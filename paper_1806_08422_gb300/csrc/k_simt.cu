@@ -235,6 +235,119 @@ csr_kernel(CsrProblem pb, RunParams rp) {
   readout<T, RC>(cur, n, r0, R, rp.signs, rp.s_out);
 }
 
+// ----------------------------------------------------------------------------
+// FP32 dense path for large n: one launch per step of Algorithm 1.  Each CTA
+// computes a 128-spin x 64-replica tile of P = J S with a register-blocked CUDA-core
+// GEMM (8 x 4 outputs per thread, 16-deep K slices staged in shared memory; J is read
+// by rows because it is symmetric) and applies the rest of the step to its tile.
+// The state lives in two global FP32 buffers S[2][n][ld] (replicas contiguous).
+// ----------------------------------------------------------------------------
+constexpr int kTBM = 128, kTBN = 64, kTBK = 16;
+
+struct TiledF32Step {
+  int n, R, ld, t;
+  const float* J;
+  const float* h32;
+  const float* inv_d32;
+  const float* S_cur;
+  float* S_next;
+  const double* T;
+  float sigma_ns, alpha, one_m_alpha;
+  NoiseKey key;
+  uint32_t stream;
+  double* phi_out;
+};
+
+__global__ void __launch_bounds__(256) dense_tiled_f32_step_kernel(TiledF32Step a) {
+  __shared__ __align__(16) float As[kTBK][kTBM];
+  __shared__ __align__(16) float Bs[kTBK][kTBN];
+  __shared__ float s_inv_T;
+  const int n = a.n;
+  const int i0 = blockIdx.x * kTBM, r0 = blockIdx.y * kTBN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x == 0) s_inv_T = static_cast<float>(1.0 / a.T[a.t]);
+  float acc[8][4];
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
+  for (int k0 = 0; k0 < n; k0 += kTBK) {
+#pragma unroll
+    for (int e = threadIdx.x; e < kTBK * kTBM; e += 256) {
+      const int kk = e / kTBM, ii = e % kTBM, k = k0 + kk, i = i0 + ii;
+      As[kk][ii] = (k < n && i < n) ? __ldg(a.J + static_cast<int64_t>(k) * n + i) : 0.0f;
+    }
+#pragma unroll
+    for (int e = threadIdx.x; e < kTBK * kTBN; e += 256) {
+      const int kk = e / kTBN, rr = e % kTBN, k = k0 + kk, r = r0 + rr;
+      Bs[kk][rr] = (k < n && r < a.ld) ? a.S_cur[static_cast<int64_t>(k) * a.ld + r] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[m][k] = fmaf(av[m], bb[k], acc[m][k]);
+    }
+    __syncthreads();
+  }
+  const float inv_T = s_inv_T;
+  const int r = r0 + tx * 4;
+  if (r >= a.ld) return;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = i0 + ty * 8 + m;
+    if (i >= n) continue;
+    const float4 z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r >> 2), static_cast<uint32_t>(a.t),
+                                            static_cast<uint32_t>(i)));
+    const float4 so = *reinterpret_cast<const float4*>(a.S_cur + static_cast<int64_t>(i) * a.ld + r);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    const float sv[4] = {so.x, so.y, so.z, so.w};
+    const float hi = a.h32[i], inv_di = a.inv_d32[i];
+    float out[4], phi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float P = hi + acc[m][k];
+      phi[k] = fmaf(a.sigma_ns, zz[k], P * inv_di);
+      out[k] = fmaf(a.alpha, -tanhf(phi[k] * inv_T), a.one_m_alpha * sv[k]);
+    }
+    *reinterpret_cast<float4*>(a.S_next + static_cast<int64_t>(i) * a.ld + r) = make_float4(out[0], out[1], out[2], out[3]);
+    if (a.phi_out != nullptr) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (r + k < a.R) a.phi_out[static_cast<int64_t>(r + k) * n + i] = static_cast<double>(phi[k]);
+    }
+  }
+}
+
+// S[0] := s0 (or 0) in the [n][ld] layout; replicas beyond R are zero.
+__global__ void tiled_f32_init_kernel(int n, int R, int ld, const double* s0, float* S) {
+  const int64_t total = static_cast<int64_t>(n) * ld;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / ld), r = static_cast<int>(e % ld);
+    S[e] = (s0 != nullptr && r < R) ? static_cast<float>(s0[static_cast<int64_t>(r) * n + i]) : 0.0f;
+  }
+}
+
+// Readout (Algorithm 1 lines 13-15) of the [n][ld] state into replica-major signs.
+__global__ void tiled_f32_readout_kernel(int n, int R, int ld, const float* S, int8_t* signs, double* s_out) {
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e / n), i = static_cast<int>(e % n);
+    const float s = S[static_cast<int64_t>(i) * ld + r];
+    signs[e] = s >= 0.0f ? int8_t(1) : int8_t(-1);
+    if (s_out != nullptr) s_out[e] = static_cast<double>(s);
+  }
+}
+
 int max_smem_optin() {
   static int v = -1;
   if (v < 0) {
@@ -320,6 +433,50 @@ int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp
     case 4: return launch_dense_rc<float, 4>(pb, rp, st);
     default: return launch_dense_rc<float, 8>(pb, rp, st);
   }
+}
+
+int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas) {
+  const int64_t ld = (replicas + 3) / 4 * 4;
+  return 2 * static_cast<int64_t>(n) * ld * 4;
+}
+
+int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, float* ws, cudaStream_t st) {
+  const int n = pb.n, R = rp.replicas;
+  const int ld = (R + 3) / 4 * 4;
+  float* S0 = ws;
+  float* S1 = ws + static_cast<int64_t>(n) * ld;
+  const int64_t total = static_cast<int64_t>(n) * ld;
+  const int gi = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8192));
+  tiled_f32_init_kernel<<<std::max(gi, 1), 256, 0, st>>>(n, R, ld, rp.s0, S0);
+  count_launch();
+  TiledF32Step a{};
+  a.n = n;
+  a.R = R;
+  a.ld = ld;
+  a.J = static_cast<const float*>(pb.J);
+  a.h32 = static_cast<const float*>(pb.h);
+  a.inv_d32 = pb.inv_d32;
+  a.T = rp.T;
+  a.sigma_ns = static_cast<float>(rp.sigma * rp.noise_sign);
+  a.alpha = static_cast<float>(rp.alpha);
+  a.one_m_alpha = static_cast<float>(1.0 - rp.alpha);
+  a.key = make_noise_key(rp.seed);
+  a.stream = rp.stream_id;
+  const dim3 grid((n + kTBM - 1) / kTBM, (ld + kTBN - 1) / kTBN);
+  for (int t = 0; t < rp.t_f; ++t) {
+    a.t = t;
+    a.S_cur = (t & 1) ? S1 : S0;
+    a.S_next = (t & 1) ? S0 : S1;
+    a.phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
+    dense_tiled_f32_step_kernel<<<grid, 256, 0, st>>>(a);
+  }
+  count_launch(static_cast<uint64_t>(rp.t_f));
+  const float* Sfin = (rp.t_f & 1) ? S1 : S0;
+  const int64_t tot2 = static_cast<int64_t>(n) * R;
+  const int go = static_cast<int>(std::min<int64_t>((tot2 + 255) / 256, 8192));
+  tiled_f32_readout_kernel<<<std::max(go, 1), 256, 0, st>>>(n, R, ld, Sfin, rp.signs, rp.s_out);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "tiled FP32 kernels");
 }
 
 int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,

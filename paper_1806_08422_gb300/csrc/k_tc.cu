@@ -4,16 +4,20 @@
 // The coupling product of line 6 over all replicas is the GEMM P = J S (J: n x n,
 // S: n x R); CTA (b, c) owns the output tile of spins [128 b, 128 b + 128) and
 // replicas [BN c, BN c + BN) for the whole run:
-//   - warp 0 (one lane) streams 64-wide K slices of J's row block and of S's
-//     replica block into a STAGES-deep shared-memory ring with TMA (128-byte
-//     swizzle), gated by per-tile "epoch" flags of the producing CTAs;
+//   - warp 0 streams 64-wide K slices of J's row block and of S's replica block
+//     into a STAGES-deep shared-memory ring with TMA (128-byte swizzle); the J
+//     slices of a step start before the step's state is published, the S slices
+//     after the whole warp has seen every row block's epoch flag of the replica
+//     block reach the step;
 //   - warp 1 (one lane) issues tcgen05.mma (M = 128, N = BN, K = 16) into a TMEM
 //     accumulator, releasing ring slots and the accumulator with tcgen05.commit;
-//   - warps 2..9 read the accumulator with tcgen05.ld and fuse the rest of the
-//     step: normalisation by d_i, the Philox/Box-Muller draw, -tanh(Phi/T_t) and
-//     the alpha-mix into the FP32 master state, which stays in TMEM for the whole
-//     run (line 10); the new state is written in BF16 to the next of two global S
-//     buffers (L2-resident) and published by bumping the tile's epoch flag.
+//   - warps 2..17 first draw the step's noise (Philox/Box-Muller, independent of
+//     the state) while the tensor core works and park sigma*z in TMEM; once the
+//     accumulator is complete they read it with tcgen05.ld and finish the step:
+//     normalisation by d_i, -tanh(Phi/T_t) and the alpha-mix into the FP32 master
+//     state, which stays in TMEM for the whole run (line 10); the new state is
+//     written in BF16 to the next of two global S buffers (L2-resident) and
+//     published by bumping the tile's epoch flag.
 // Step t+1's slices of row block b' are loaded only after tile (b', c) has
 // published step t, which realises the synchronous update of Algorithm 1
 // (every Phi from the old state) without a grid-wide barrier: only the CTAs of
@@ -41,7 +45,7 @@ namespace {
 
 constexpr int kBM = 128;               // spins per tile (TMEM lanes)
 constexpr int kBK = 64;                // K slice: 64 BF16 = one 128-byte swizzle row
-constexpr int kEpiWarps = 8;           // two warps per TMEM lane quarter
+constexpr int kEpiWarps = 16;          // four warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint64_t kDrainNs = 200000000ull;
@@ -98,16 +102,26 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SharedCt
   }
 }
 
-__device__ __forceinline__ bool wait_flag(const uint32_t* f, uint32_t need, SharedCtl* ctl, int32_t* status) {
-  if (ptx::ld_acquire_gpu(f) >= need) return true;
+// Warp-wide wait until every row block's epoch flag of one replica block reaches
+// `need`: lane l polls row blocks l, l+32, ... in parallel (one round trip per poll
+// instead of one per row block).  Returns false (on every lane) on abort/timeout.
+__device__ __forceinline__ bool wait_group_flags(const uint32_t* f0, int nb, int stride, uint32_t need, int lane,
+                                                 SharedCtl* ctl, int32_t* status) {
   const uint64_t t0 = ptx::globaltimer_ns();
   while (true) {
-    if (ptx::ld_acquire_gpu(f) >= need) return true;
-    if (aborted(ctl)) return false;
-    if (ptx::globaltimer_ns() - t0 > kTimeoutNs) {
-      raise_abort(ctl, status);
-      return false;
+    bool mine = true;
+    for (int rb = lane; rb < nb; rb += 32) mine = mine && (ptx::ld_acquire_gpu(f0 + static_cast<int64_t>(rb) * stride) >= need);
+    if (__all_sync(0xffffffffu, mine)) return true;
+    int stop = 0;
+    if (lane == 0) {
+      if (aborted(ctl)) {
+        stop = 1;
+      } else if (ptx::globaltimer_ns() - t0 > kTimeoutNs) {
+        raise_abort(ctl, status);
+        stop = 1;
+      }
     }
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
   }
 }
 
@@ -117,7 +131,8 @@ struct TcCfg {
   static constexpr uint32_t kABytes = kBM * 128;
   static constexpr uint32_t kBBytes = BN * 128;
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;
-  static constexpr uint32_t kTmemCols = (2 * BN <= 32) ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512)));
+  // accumulator [0, BN), FP32 master state [BN, 2BN), the step's noise [2BN, 3BN)
+  static constexpr uint32_t kTmemCols = (3 * BN <= 64 ? 64 : (3 * BN <= 128 ? 128 : (3 * BN <= 256 ? 256 : 512)));
   static constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
   static_assert(kStages <= 16, "ring too deep");
   static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN");
@@ -162,40 +177,76 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      uint32_t it = 0;
-      bool ok = true;
-      for (int t = 0; t < a.t_f && ok; ++t) {
-        const int buf = t & 1;
-        for (int kb = 0; kb < KB && ok; ++kb) {
-          int kbr = kb + 2 * b;
-          if (kbr >= KB) kbr -= KB;
-          if ((kbr & 1) == 0) {
-            ok = wait_flag(a.flags + static_cast<int64_t>(kbr >> 1) * a.rbk + c, static_cast<uint32_t>(t + 1), &ctl,
-                           a.status);
-            if (!ok) break;
-            ptx::fence_proxy_async_global();
-          }
+    // Per step: claim the first ring slots and start their J slices at once (J
+    // does not depend on the previous step), wait with the whole warp until every
+    // row block of this replica block has published the step's state, then issue
+    // the S slices of the claimed slots and stream the rest of the step.
+    const int pre = KB < kStages ? KB : kStages;
+    uint32_t it = 0;        // ring iterations whose J and S copies are both issued
+    int pending = 0;        // claimed slots with only the J copy issued
+    bool ok = true;
+    auto kslice = [&](int kb) {
+      int kbr = kb + 2 * b;
+      return kbr >= KB ? kbr - KB : kbr;
+    };
+    for (int t = 0; t < a.t_f && ok; ++t) {
+      const int buf = t & 1;
+      const int sy = buf * a.r_pad + c * BN;
+      if (lane == 0) {
+        for (int kb = 0; kb < pre; ++kb) {
+          const uint32_t k = it + kb, stage = k % kStages, phase = (k / kStages) & 1u;
+          ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, a.status);
+          if (!ok) break;
+          const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
+          ptx::mbar_arrive_expect_tx(full, Cfg::kStageBytes);
+          ptx::tma_load_2d(ring + stage * Cfg::kStageBytes, &tmJ, kslice(kb) * kBK, b * kBM, full);
+          pending = kb + 1;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      ok = wait_group_flags(a.flags + c, a.n_pad / kBM, a.rbk, static_cast<uint32_t>(t + 1), lane, &ctl, a.status);
+      // each lane acquired its own row blocks' flags; the warp barrier orders those
+      // acquires before lane 0's copies (memory ordering among the warp's threads)
+      __syncwarp();
+      if (lane == 0) {
+        if (ok) ptx::fence_proxy_async_global();
+        // the S halves of the claimed slots (also on abort, so that their barriers complete)
+        for (int kb = 0; kb < pending; ++kb) {
+          const uint32_t k = it + kb, stage = k % kStages;
+          ptx::tma_load_2d(ring + stage * Cfg::kStageBytes + Cfg::kABytes, &tmS, kslice(kb) * kBK, sy,
+                           ptx::smem_u32(&ctl.full[stage]));
+        }
+        it += pending;
+        pending = 0;
+        for (int kb = pre; kb < KB && ok; ++kb) {
           const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
           ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, a.status);
           if (!ok) break;
           const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
           const uint32_t sA = ring + stage * Cfg::kStageBytes;
           ptx::mbar_arrive_expect_tx(full, Cfg::kStageBytes);
-          ptx::tma_load_2d(sA, &tmJ, kbr * kBK, b * kBM, full);
-          ptx::tma_load_2d(sA + Cfg::kABytes, &tmS, kbr * kBK, buf * a.r_pad + c * BN, full);
+          ptx::tma_load_2d(sA, &tmJ, kslice(kb) * kBK, b * kBM, full);
+          ptx::tma_load_2d(sA + Cfg::kABytes, &tmS, kslice(kb) * kBK, sy, full);
           ++it;
         }
       }
-      if (!ok) {
-        // drain: wait (bounded) until every copy this thread issued has landed
-        const uint32_t last = it;
-        for (uint32_t k = (last > static_cast<uint32_t>(kStages) ? last - kStages : 0u); k < last; ++k) {
-          const uint32_t stage = k % kStages, phase = (k / kStages) & 1u;
-          const uint64_t t0 = ptx::globaltimer_ns();
-          while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.full[stage]), phase) &&
-                 ptx::globaltimer_ns() - t0 < kDrainNs) {
-          }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    }
+    if (!ok && lane == 0) {
+      // J-only slots claimed before a failed wait get their S copy so their barriers complete
+      for (int kb = 0; kb < pending; ++kb) {
+        const uint32_t k = it + kb, stage = k % kStages;
+        ptx::tma_load_2d(ring + stage * Cfg::kStageBytes + Cfg::kABytes, &tmS, kslice(kb) * kBK, c * BN,
+                         ptx::smem_u32(&ctl.full[stage]));
+      }
+      it += pending;
+      // drain: wait (bounded) until every copy this thread issued has landed
+      const uint32_t last = it;
+      for (uint32_t k = (last > static_cast<uint32_t>(kStages) ? last - kStages : 0u); k < last; ++k) {
+        const uint32_t stage = k % kStages, phase = (k / kStages) & 1u;
+        const uint64_t t0 = ptx::globaltimer_ns();
+        while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.full[stage]), phase) && ptx::globaltimer_ns() - t0 < kDrainNs) {
         }
       }
     }
@@ -241,9 +292,12 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // Warp e serves TMEM lane quarter q = warp % 4 (spins 32q..32q+31 of the tile)
+    // and column group e / 4 (BN/4 replicas), 16 columns per tcgen05.ld.
+    constexpr int kCW = BN / 4;
     const int e = warp - 2;
-    const int q = warp & 3;               // TMEM lane quarter this warp may access
-    const int col0 = (e >> 2) * (BN / 2); // column half
+    const int q = warp & 3;
+    const int col0 = (e >> 2) * kCW;
     const int i = b * kBM + q * 32 + lane;
     const bool valid = i < a.n;
     const float inv_d = a.inv_d32[i];
@@ -251,19 +305,20 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
     const int rbase = c * BN + col0;
     const size_t plane = static_cast<size_t>(a.r_pad) * a.n_pad;
-    uint32_t v[32], m[32];
+    const RoundKeys rk = make_round_keys(a.key);
+    uint32_t v[16], m[16];
 
     // initial state (line 2, or the given s0) -> master in TMEM and BF16 buffer 0
-    for (int cc = 0; cc < BN / 2; cc += 32) {
+    for (int cc = 0; cc < kCW; cc += 16) {
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
+      for (int k = 0; k < 16; ++k) {
         const int r = rbase + cc + k;
         float s = 0.0f;
         if (a.s0 != nullptr && valid && r < a.replicas) s = static_cast<float>(a.s0[static_cast<int64_t>(r) * a.n + i]);
         m[k] = __float_as_uint(s);
         a.S16[static_cast<size_t>(r) * a.n_pad + i] = __float2bfloat16_rn(s);
       }
-      ptx::tmem_st32(lane_base + BN + col0 + cc, m);
+      ptx::tmem_st16(lane_base + BN + col0 + cc, m);
     }
     ptx::tmem_wait_st();
     ptx::fence_proxy_async_global();
@@ -277,44 +332,61 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
       return __all_sync(0xffffffffu, got);
     };
     bool ok = epi_meet(0);
-    if (ok && e == 0 && lane == 0) {
-      __threadfence();
-      ptx::st_release_gpu(a.flags + static_cast<int64_t>(b) * a.rbk + c, 1u);
-    }
+    if (ok && e == 0 && lane == 0) ptx::st_release_gpu(a.flags + static_cast<int64_t>(b) * a.rbk + c, 1u);
 
     for (int t = 0; t < a.t_f && ok; ++t) {
+      float inv_T = 0.0f;
+      if (lane == 0) inv_T = 1.0f / static_cast<float>(a.T[t]);  // one FP64 load+convert per warp
+      inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
+      const bool write_phi = (t == a.t_f - 1) && a.phi_out != nullptr;
+      __nv_bfloat16* Snext = a.S16 + static_cast<size_t>((t + 1) & 1) * plane;
+      // (A) the step's Gaussian draws do not depend on the state: generate them while
+      // the tensor core computes this step's product, and park them in TMEM
+      for (int cc = 0; cc < kCW; cc += 16) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int r4 = rbase + cc + 4 * g;
+          const float4 z = gauss4_f32_fast(philox4x32_10_rk(
+              make_uint4(static_cast<uint32_t>(r4 >> 2), static_cast<uint32_t>(t), static_cast<uint32_t>(i), a.stream),
+              rk));
+          v[4 * g + 0] = __float_as_uint(a.sigma_ns * z.x);
+          v[4 * g + 1] = __float_as_uint(a.sigma_ns * z.y);
+          v[4 * g + 2] = __float_as_uint(a.sigma_ns * z.z);
+          v[4 * g + 3] = __float_as_uint(a.sigma_ns * z.w);
+        }
+        ptx::tmem_st16(lane_base + 2 * BN + col0 + cc, v);
+      }
+      ptx::tmem_wait_st();
+      // (B) the update, once the product is in TMEM
       ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.acc_full), static_cast<uint32_t>(t & 1), &ctl, a.status));
       if (!ok) break;
       ptx::tc_fence_after();
-      const double Td = a.T[t];
-      const float inv_T = static_cast<float>(1.0 / Td);
-      const bool last = (t == a.t_f - 1);
-      __nv_bfloat16* Snext = a.S16 + static_cast<size_t>((t + 1) & 1) * plane;
-      for (int cc = 0; cc < BN / 2; cc += 32) {
-        ptx::tmem_ld32(lane_base + col0 + cc, v);
-        ptx::tmem_ld32(lane_base + BN + col0 + cc, m);
+      for (int cc = 0; cc < kCW; cc += 16) {
+        uint32_t zn[16];
+        ptx::tmem_ld16(lane_base + col0 + cc, v);
+        ptx::tmem_ld16(lane_base + BN + col0 + cc, m);
+        ptx::tmem_ld16(lane_base + 2 * BN + col0 + cc, zn);
         ptx::tmem_wait_ld();
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          const int r4 = rbase + cc + 4 * g;
-          const float4 z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r4 >> 2),
-                                                  static_cast<uint32_t>(t), static_cast<uint32_t>(i)));
-          const float zz[4] = {z.x, z.y, z.z, z.w};
+        for (int k = 0; k < 16; ++k) {
+          const float P = __uint_as_float(v[k]) + hi;
+          const float phi = fmaf(P, inv_d, __uint_as_float(zn[k]));
+          const float sh = -ptx::tanh_approx(phi * inv_T);
+          const float s_new = fmaf(a.alpha, sh, a.one_m_alpha * __uint_as_float(m[k]));
+          m[k] = __float_as_uint(s_new);
+          v[k] = __float_as_uint(phi);
+        }
+        if (write_phi) {  // last step of a debug run only (warp-uniform branch)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int col = 4 * g + k;
-            const float P = __uint_as_float(v[col]) + hi;
-            const float phi = fmaf(a.sigma_ns, zz[k], P * inv_d);
-            const float sh = -tanhf(phi * inv_T);
-            const float s_new = fmaf(a.alpha, sh, a.one_m_alpha * __uint_as_float(m[col]));
-            m[col] = __float_as_uint(s_new);
-            if (last && a.phi_out != nullptr && valid && r4 + k < a.replicas)
-              a.phi_out[static_cast<int64_t>(r4 + k) * a.n + i] = static_cast<double>(phi);
+          for (int k = 0; k < 16; ++k) {
+            const int r = rbase + cc + k;
+            if (valid && r < a.replicas)
+              a.phi_out[static_cast<int64_t>(r) * a.n + i] = static_cast<double>(__uint_as_float(v[k]));
           }
         }
-        ptx::tmem_st32(lane_base + BN + col0 + cc, m);
+        ptx::tmem_st16(lane_base + BN + col0 + cc, m);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < 16; ++k) {
           const int r = rbase + cc + k;
           Snext[static_cast<size_t>(r) * a.n_pad + i] =
               valid ? __float2bfloat16_rn(__uint_as_float(m[k])) : __float2bfloat16_rn(0.0f);
@@ -327,18 +399,18 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
       ptx::fence_proxy_async_global();
       ok = epi_meet(static_cast<uint32_t>(t + 1));
       if (!ok) break;
-      if (e == 0 && lane == 0) {
-        __threadfence();
+      // The release store publishes every epilogue thread's state writes: they
+      // happen before it through the rendezvous above (cumulativity).
+      if (e == 0 && lane == 0)
         ptx::st_release_gpu(a.flags + static_cast<int64_t>(b) * a.rbk + c, static_cast<uint32_t>(t + 2));
-      }
     }
     // readout (lines 13-15): sign of the FP32 master state, zero reads as +1
     if (__all_sync(0xffffffffu, ok && !aborted(&ctl))) {
-      for (int cc = 0; cc < BN / 2; cc += 32) {
-        ptx::tmem_ld32(lane_base + BN + col0 + cc, m);
+      for (int cc = 0; cc < kCW; cc += 16) {
+        ptx::tmem_ld16(lane_base + BN + col0 + cc, m);
         ptx::tmem_wait_ld();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < 16; ++k) {
           const int r = rbase + cc + k;
           if (valid && r < a.replicas) {
             const float s = __uint_as_float(m[k]);
@@ -473,6 +545,7 @@ int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, c
   if (pb.n_pad % kBM != 0) return set_error(NMFA_EINVAL, "tensor path: n_pad must be a multiple of 128");
   return pick_bn(rp.replicas) == 64 ? launch_tc_bn<64>(pb, rp, ws, st) : launch_tc_bn<128>(pb, rp, ws, st);
 }
+
 
 // ----------------------------------------------------------------------------
 // Scratch without allocation, for nmfa_run_device_noalloc.

@@ -480,7 +480,12 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
         pb.h = f64 ? static_cast<const void*>(p->h64) : static_cast<const void*>(p->h32);
         pb.d = p->d64;
         pb.inv_d32 = p->inv_d32;
-        rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
+        if (!f64 && p->n >= kTiledF32MinN && p->replicas_per_cta == 0) {
+          if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas))))) return rc;
+          rc = launch_dense_tiled_f32(pb, rp, static_cast<float*>(p->ws.p), st);
+        } else {
+          rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
+        }
       }
       break;
     }

@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/nmfa.h"
+#include "nmfa.h"
 
 namespace nmfa {
 
@@ -47,6 +47,12 @@ struct DenseSimtProblem {
 };
 int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
                       cudaStream_t st, int replicas_per_cta);
+// FP32 dense path for large n: per-step register-blocked GEMM + fused update, state
+// in a caller-provided scratch of tiled_f32_workspace_bytes(n, R) bytes.
+int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas);
+int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, float* ws, cudaStream_t st);
+// n from which the FP32 dense path switches to the tiled per-step kernel.
+constexpr int32_t kTiledF32MinN = 512;
 
 // ---- CUDA-core CSR path (FP32 / FP64) ---------------------------------------
 struct CsrProblem {

@@ -26,7 +26,7 @@ def _rand_state(R, n, seed):
 
 # ---------------------------------------------------------------- single step
 @pytest.mark.parametrize("prec", DENSE)
-@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64)])
+@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64), (700, 130)])
 def test_single_step_phi(prec, n, R):
     J = inst.sk(n, 100 + n) if n > 1 else np.zeros((1, 1))
     h = inst.random_fields(n, 0.5, 7) if prec != "bf16" else None
