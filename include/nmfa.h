@@ -178,6 +178,53 @@ int nmfa_debug_run(nmfa_problem* p, const double* T_dev, int32_t t_f, double sig
                    double* phi_out_dev, int8_t* signs_dev, double* energy_dev,
                    int64_t* energy_i64_dev, void* cuda_stream);
 
+/*
+ * Batches -- many tensor-path runs in ONE persistent launch (ragged batches of
+ * instances of different sizes and replica counts).  Each job is an independent
+ * Algorithm 1 run on its own NMFA_BF16 problem with its own schedule and noise
+ * stream; its results are bit-identical to running it alone with nmfa_run_device
+ * (the tiling of a run depends only on its own shape, and the noise counters are
+ * the run's logical (replica, step, spin) indices).
+ */
+typedef struct {
+  const double* T_dev;     /* device, t_f float64 temperatures */
+  int32_t t_f;
+  double sigma, alpha;
+  int32_t replicas;
+  uint64_t seed;
+  uint32_t stream_id;
+  int8_t* signs_dev;       /* device R*n int8, or NULL (batch keeps scratch) */
+  double* energy_dev;      /* device R float64, or NULL */
+  int64_t* energy_i64_dev; /* device R int64, or NULL (integer problems only) */
+} nmfa_job;
+
+typedef struct nmfa_batch nmfa_batch;
+
+#define NMFA_BATCH_GRAPH 1    /* capture the batch's launches in a CUDA graph at creation */
+#define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128) per job by timing */
+#define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
+
+/* Plans the batch (tiles of 128 spins x 64 or 128 replicas; the CTAs of one replica
+ * block are co-scheduled on the persistent grid by list scheduling), allocates its
+ * workspace, uploads the plan and, with NMFA_BATCH_GRAPH, captures the launch
+ * sequence as a CUDA graph.  The problems and every device buffer named in `jobs`
+ * must stay valid while the batch exists; each launch overwrites the outputs. */
+int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32_t count,
+                      int32_t options, nmfa_batch** out);
+/* Enqueues one execution of the whole batch on `cuda_stream` (ordered after the
+ * batch's previous execution). */
+int nmfa_batch_launch(nmfa_batch* b, void* cuda_stream);
+/* Waits for the last execution; NMFA_ETIMEOUT if a device-side wait gave up. */
+int nmfa_batch_sync(nmfa_batch* b);
+/* Persistent grid size, number of replica-block groups, workspace bytes. */
+int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes);
+void nmfa_batch_destroy(nmfa_batch* b);
+
+/* Autotuner entry: the replicas-per-tile (64 or 128) the tensor path would use for
+ * `replicas` replicas of this problem, measured once per (n rounded to 128,
+ * replicas) and cached for the process. */
+int nmfa_autotune_bn(nmfa_problem* p, int32_t replicas, int32_t* bn);
+
 /* Problem facts: spins, precision, 1 if h and J are integer-valued, device bytes
  * held (any pointer may be NULL). */
 int nmfa_problem_info(const nmfa_problem* p, int32_t* n, int32_t* precision,

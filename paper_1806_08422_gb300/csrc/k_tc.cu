@@ -17,7 +17,7 @@
 //     normalisation by d_i, -tanh(Phi/T_t) and the alpha-mix into the FP32 master
 //     state, which stays in TMEM for the whole run (line 10); the new state is
 //     written in BF16 to the next of two global S buffers (L2-resident) and
-//     published by bumping the tile's epoch flag.
+//     published by each warp's release increment of the tile's epoch counter.
 // Step t+1's slices of row block b' are loaded only after tile (b', c) has
 // published step t, which realises the synchronous update of Algorithm 1
 // (every Phi from the old state) without a grid-wide barrier: only the CTAs of
@@ -33,7 +33,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "nmfa_device.cuh"
 #include "nmfa_internal.h"
@@ -45,35 +47,56 @@ namespace {
 
 constexpr int kBM = 128;               // spins per tile (TMEM lanes)
 constexpr int kBK = 64;                // K slice: 64 BF16 = one 128-byte swizzle row
-constexpr int kEpiWarps = 16;          // four warps per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kBNMax = 128;            // replicas per tile (MMA N), 64 or 128 per group
+// Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
+// tile of BN replicas takes BN / 8 warps (16 for 128-replica tiles, 8 for 64).
+template <int BN>
+struct TcShape {
+  static constexpr int kEpiWarps = BN / 8;
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+};
+constexpr int kColsPerWarp = 32;
+constexpr int kStages = 6;
+constexpr uint32_t kABytes = kBM * 128;
+constexpr uint32_t kStageBytes = kABytes + kBNMax * 128;
+// TMEM columns: accumulator [0, 128), FP32 master state [128, 256), noise [256, 384)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColMaster = kBNMax;
+constexpr uint32_t kColNoise = 2 * kBNMax;
+constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
+// A CTA that reaches a new group early waits for the group's other CTAs to finish
+// the groups scheduled before it; that first wait gets a longer bound.
+constexpr uint64_t kStartTimeoutNs = 20000000000ull;
 constexpr uint64_t kDrainNs = 200000000ull;
 
-struct TcArgs {
-  int32_t n, n_pad, r_pad, replicas, t_f, c_offset, rbk;
+// One replica block of one instance: the CTAs that exchange state every step.
+struct __align__(64) TcGroup {
+  CUtensorMap tmJ;        // BF16 J of the instance, [n_pad][n_pad], box 64 x 128
+  CUtensorMap tmS;        // this group's state buffers, [2 * bn][n_pad], box 64 x bn
   const float* inv_d32;
   const float* h32;
   const double* T;
-  float sigma_ns, alpha, one_m_alpha;
-  NoiseKey key;
-  uint32_t stream;
-  const double* s0;
+  const double* s0;       // instance-level (replica-major, n per replica) or null
   double* s_out;
   double* phi_out;
   int8_t* signs;
-  __nv_bfloat16* S16;   // [2][r_pad][n_pad]
-  uint32_t* flags;      // [n_pad/128][rbk]
-  int32_t* status;
+  __nv_bfloat16* S16;     // [2][bn][n_pad]
+  uint32_t* flags;        // [nb] epoch counters
+  int32_t n, n_pad, bn, replicas, r0, t_f;
+  float sigma_ns, alpha, one_m_alpha;
+  uint32_t seed_lo, seed_hi, stream;
+};
+struct TcItem {
+  int32_t group, b;
 };
 
 struct SharedCtl {
-  uint64_t full[16];
-  uint64_t empty[16];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
   uint64_t acc_full;
   uint64_t acc_empty;
   uint64_t drain;
-  uint64_t epi_sync;   // rendezvous of the epilogue warps (bounded, abort-aware)
   uint32_t tmem_slot;
   int32_t abort_flag;
 };
@@ -102,21 +125,21 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SharedCt
   }
 }
 
-// Warp-wide wait until every row block's epoch flag of one replica block reaches
-// `need`: lane l polls row blocks l, l+32, ... in parallel (one round trip per poll
-// instead of one per row block).  Returns false (on every lane) on abort/timeout.
-__device__ __forceinline__ bool wait_group_flags(const uint32_t* f0, int nb, int stride, uint32_t need, int lane,
-                                                 SharedCtl* ctl, int32_t* status) {
+// Warp-wide wait until every row block's epoch counter of one group reaches
+// `need`: lane l polls row blocks l, l+32, ... in parallel.  Returns false (on every
+// lane) on abort/timeout.
+__device__ __forceinline__ bool wait_group_flags(const uint32_t* f0, int nb, uint32_t need, int lane,
+                                                 SharedCtl* ctl, int32_t* status, uint64_t limit_ns) {
   const uint64_t t0 = ptx::globaltimer_ns();
   while (true) {
     bool mine = true;
-    for (int rb = lane; rb < nb; rb += 32) mine = mine && (ptx::ld_acquire_gpu(f0 + static_cast<int64_t>(rb) * stride) >= need);
+    for (int rb = lane; rb < nb; rb += 32) mine = mine && (ptx::ld_acquire_gpu(f0 + rb) >= need);
     if (__all_sync(0xffffffffu, mine)) return true;
     int stop = 0;
     if (lane == 0) {
       if (aborted(ctl)) {
         stop = 1;
-      } else if (ptx::globaltimer_ns() - t0 > kTimeoutNs) {
+      } else if (ptx::globaltimer_ns() - t0 > limit_ns) {
         raise_abort(ctl, status);
         stop = 1;
       }
@@ -125,31 +148,159 @@ __device__ __forceinline__ bool wait_group_flags(const uint32_t* f0, int nb, int
   }
 }
 
+// The tensor maps live in global memory (written by an earlier kernel); make the
+// tensormap proxy see those writes before the first copy that uses them.
+__device__ __forceinline__ void acquire_tensormap(const void* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+               : "memory");
+}
+
+// Epilogue warps' work for one item (one 128-spin tile of one group), from the
+// initial state through t_f steps to the readout.  Warp e serves TMEM lane quarter
+// q = (e + 2) % 4 (spins 32q..32q+31 of the tile) and column group e / 4 (32
+// replicas), 16 columns per tcgen05.ld.  `gstep` counts the CTA's steps across items
+// (the parity of the accumulator barriers).  Returns false on abort.
 template <int BN>
-struct TcCfg {
-  static constexpr int kStages = BN >= 128 ? 6 : 8;
-  static constexpr uint32_t kABytes = kBM * 128;
-  static constexpr uint32_t kBBytes = BN * 128;
-  static constexpr uint32_t kStageBytes = kABytes + kBBytes;
-  // accumulator [0, BN), FP32 master state [BN, 2BN), the step's noise [2BN, 3BN)
-  static constexpr uint32_t kTmemCols = (3 * BN <= 64 ? 64 : (3 * BN <= 128 ? 128 : (3 * BN <= 256 ? 256 : 512)));
-  static constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
-  static_assert(kStages <= 16, "ring too deep");
-  static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "BN");
-};
+__device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
+                                              SharedCtl* ctl, int32_t* status, uint32_t& gstep) {
+  constexpr int kCW = kColsPerWarp;
+  const int q = (e + 2) & 3;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
+  const int n = g->n, n_pad = g->n_pad, t_f = g->t_f, R = g->replicas;
+  const int col0 = (e >> 2) * kCW;
+  const int i = b * kBM + q * 32 + lane;
+  const bool valid = i < n;
+  const float inv_d = g->inv_d32[i];
+  const float hi = g->h32[i];
+  const int rbase = g->r0 + col0;  // replica index (of the instance) of column col0
+  const size_t plane = static_cast<size_t>(BN) * n_pad;
+  const RoundKeys rk = make_round_keys(NoiseKey{g->seed_lo, g->seed_hi});
+  const float sigma_ns = g->sigma_ns, alpha = g->alpha, oma = g->one_m_alpha;
+  const uint32_t stream = g->stream;
+  const double* T = g->T;
+  double* phi_out = g->phi_out;
+  __nv_bfloat16* S16 = g->S16;
+  uint32_t* my_flag = g->flags + b;
+  uint32_t v[16], m[16];
+
+  // initial state (line 2, or the given s0) -> master in TMEM and BF16 buffer 0
+  const double* s0 = g->s0;
+#pragma unroll 1
+  for (int cc = 0; cc < kCW; cc += 16) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = rbase + cc + k;
+      float s = 0.0f;
+      if (s0 != nullptr && valid && r < R) s = static_cast<float>(s0[static_cast<int64_t>(r) * n + i]);
+      m[k] = __float_as_uint(s);
+      S16[static_cast<size_t>(col0 + cc + k) * n_pad + i] = __float2bfloat16_rn(s);
+    }
+    ptx::tmem_st16(lane_base + kColMaster + col0 + cc, m);
+  }
+  ptx::tmem_wait_st();
+  // Publication: every epilogue warp adds 1 to its tile's epoch counter with a
+  // release reduction once its lanes' state writes are done (the warp barrier orders
+  // the lanes' writes before lane 0's release), so the counter reaches
+  // (epilogue warps) * (t + 1) when the whole tile of state S_t is visible.
+  ptx::fence_proxy_async_global();
+  __syncwarp();
+  if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
+
+  for (int t = 0; t < t_f; ++t, ++gstep) {
+    float inv_T = 0.0f;
+    if (lane == 0) inv_T = 1.0f / static_cast<float>(T[t]);  // one FP64 load+convert per warp
+    inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
+    __nv_bfloat16* Snext = S16 + static_cast<size_t>((t + 1) & 1) * plane;
+    // (A) the step's Gaussian draws do not depend on the state: generate them while
+    // the tensor core computes this step's product, and park them in TMEM
+#pragma unroll 1
+    for (int cc = 0; cc < kCW; cc += 16) {
+#pragma unroll
+      for (int gq = 0; gq < 4; ++gq) {
+        const int r4 = rbase + cc + 4 * gq;
+        const float4 z = gauss4_f32_fast(philox4x32_10_rk(
+            make_uint4(static_cast<uint32_t>(r4 >> 2), static_cast<uint32_t>(t), static_cast<uint32_t>(i), stream), rk));
+        v[4 * gq + 0] = __float_as_uint(sigma_ns * z.x);
+        v[4 * gq + 1] = __float_as_uint(sigma_ns * z.y);
+        v[4 * gq + 2] = __float_as_uint(sigma_ns * z.z);
+        v[4 * gq + 3] = __float_as_uint(sigma_ns * z.w);
+      }
+      ptx::tmem_st16(lane_base + kColNoise + col0 + cc, v);
+    }
+    ptx::tmem_wait_st();
+    // (B) the update, once the product is in TMEM
+    if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
+    ptx::tc_fence_after();
+    const bool write_phi = (t == t_f - 1) && phi_out != nullptr;
+#pragma unroll 1
+    for (int cc = 0; cc < kCW; cc += 16) {
+      uint32_t zn[16];
+      ptx::tmem_ld16(lane_base + col0 + cc, v);
+      ptx::tmem_ld16(lane_base + kColMaster + col0 + cc, m);
+      ptx::tmem_ld16(lane_base + kColNoise + col0 + cc, zn);
+      ptx::tmem_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float P = __uint_as_float(v[k]) + hi;
+        const float phi = fmaf(P, inv_d, __uint_as_float(zn[k]));
+        const float sh = -ptx::tanh_approx(phi * inv_T);
+        const float s_new = fmaf(alpha, sh, oma * __uint_as_float(m[k]));
+        m[k] = __float_as_uint(s_new);
+        v[k] = __float_as_uint(phi);
+      }
+      if (write_phi) {  // last step of a debug run only (warp-uniform branch)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int r = rbase + cc + k;
+          if (valid && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(__uint_as_float(v[k]));
+        }
+      }
+      ptx::tmem_st16(lane_base + kColMaster + col0 + cc, m);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        Snext[static_cast<size_t>(col0 + cc + k) * n_pad + i] =
+            valid ? __float2bfloat16_rn(__uint_as_float(m[k])) : __float2bfloat16_rn(0.0f);
+      }
+    }
+    ptx::tmem_wait_st();
+    ptx::tc_fence_before();
+    __syncwarp();
+    if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->acc_empty));
+    ptx::fence_proxy_async_global();
+    __syncwarp();
+    if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
+  }
+  // readout (lines 13-15): sign of the FP32 master state, zero reads as +1
+  if (!__all_sync(0xffffffffu, !aborted(ctl))) return false;
+  int8_t* signs = g->signs;
+  double* s_out = g->s_out;
+#pragma unroll 1
+  for (int cc = 0; cc < kCW; cc += 16) {
+    ptx::tmem_ld16(lane_base + kColMaster + col0 + cc, m);
+    ptx::tmem_wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = rbase + cc + k;
+      if (valid && r < R) {
+        const float s = __uint_as_float(m[k]);
+        signs[static_cast<int64_t>(r) * n + i] = s >= 0.0f ? int8_t(1) : int8_t(-1);
+        if (s_out != nullptr) s_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(s);
+      }
+    }
+  }
+  return true;
+}
 
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
-nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmS, TcArgs a) {
-  using Cfg = TcCfg<BN>;
-  constexpr int kStages = Cfg::kStages;
+__global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
+nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
+               int32_t* status) {
+  constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   __shared__ SharedCtl ctl;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x;
-  const int c = a.c_offset + blockIdx.y;
-  const int KB = a.n_pad / kBK;
+  const int w_begin = first[blockIdx.x], w_end = first[blockIdx.x + 1];
   const uint32_t ring = (ptx::smem_u32(smem_dyn) + 1023u) & ~1023u;
 
   if (threadIdx.x == 0) {
@@ -160,14 +311,11 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
     ptx::mbar_init(ptx::smem_u32(&ctl.acc_full), 1);
     ptx::mbar_init(ptx::smem_u32(&ctl.acc_empty), kEpiWarps);
     ptx::mbar_init(ptx::smem_u32(&ctl.drain), 1);
-    ptx::mbar_init(ptx::smem_u32(&ctl.epi_sync), kEpiWarps);
     ctl.abort_flag = 0;
     ptx::fence_mbar_init();
-    ptx::tma_prefetch_desc(&tmJ);
-    ptx::tma_prefetch_desc(&tmS);
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(&ctl.tmem_slot), Cfg::kTmemCols);
+    ptx::tmem_alloc(ptx::smem_u32(&ctl.tmem_slot), kTmemCols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -179,65 +327,83 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
     // ------------------------------------------------------------ TMA producer
     // Per step: claim the first ring slots and start their J slices at once (J
     // does not depend on the previous step), wait with the whole warp until every
-    // row block of this replica block has published the step's state, then issue
-    // the S slices of the claimed slots and stream the rest of the step.
-    const int pre = KB < kStages ? KB : kStages;
+    // row block of the group has published the step's state, then issue the S
+    // slices of the claimed slots and stream the rest of the step.
     uint32_t it = 0;        // ring iterations whose J and S copies are both issued
     int pending = 0;        // claimed slots with only the J copy issued
     bool ok = true;
-    auto kslice = [&](int kb) {
-      int kbr = kb + 2 * b;
-      return kbr >= KB ? kbr - KB : kbr;
-    };
-    for (int t = 0; t < a.t_f && ok; ++t) {
-      const int buf = t & 1;
-      const int sy = buf * a.r_pad + c * BN;
+    const void* tmS_cur = nullptr;
+    int kslice_base = 0, KB_cur = 1;
+#define NMFA_KSLICE(kb) ((kb) + kslice_base >= KB_cur ? (kb) + kslice_base - KB_cur : (kb) + kslice_base)
+    for (int w = w_begin; w < w_end && ok; ++w) {
+      const TcItem item = items[w];
+      const TcGroup* g = groups + item.group;
+      const int b = item.b, n_pad = g->n_pad, nb = n_pad / kBM, bn = g->bn, t_f = g->t_f;
+      const void* tmJ = &g->tmJ;
+      const void* tmS = &g->tmS;
+      const uint32_t* gflags = g->flags;
+      const uint32_t stage_tx = kABytes + static_cast<uint32_t>(bn) * 128u;
+      KB_cur = n_pad / kBK;
+      kslice_base = 2 * b;
+      tmS_cur = tmS;
       if (lane == 0) {
-        for (int kb = 0; kb < pre; ++kb) {
-          const uint32_t k = it + kb, stage = k % kStages, phase = (k / kStages) & 1u;
-          ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, a.status);
-          if (!ok) break;
-          const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
-          ptx::mbar_arrive_expect_tx(full, Cfg::kStageBytes);
-          ptx::tma_load_2d(ring + stage * Cfg::kStageBytes, &tmJ, kslice(kb) * kBK, b * kBM, full);
-          pending = kb + 1;
-        }
+        acquire_tensormap(tmJ);
+        acquire_tensormap(tmS);
+        ptx::tma_prefetch_desc(tmJ);
+        ptx::tma_prefetch_desc(tmS);
       }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) break;
-      ok = wait_group_flags(a.flags + c, a.n_pad / kBM, a.rbk, static_cast<uint32_t>(t + 1), lane, &ctl, a.status);
-      // each lane acquired its own row blocks' flags; the warp barrier orders those
-      // acquires before lane 0's copies (memory ordering among the warp's threads)
       __syncwarp();
-      if (lane == 0) {
-        if (ok) ptx::fence_proxy_async_global();
-        // the S halves of the claimed slots (also on abort, so that their barriers complete)
-        for (int kb = 0; kb < pending; ++kb) {
-          const uint32_t k = it + kb, stage = k % kStages;
-          ptx::tma_load_2d(ring + stage * Cfg::kStageBytes + Cfg::kABytes, &tmS, kslice(kb) * kBK, sy,
-                           ptx::smem_u32(&ctl.full[stage]));
+      const int pre = KB_cur < kStages ? KB_cur : kStages;
+      for (int t = 0; t < t_f && ok; ++t) {
+        const int sy = (t & 1) * bn;
+        if (lane == 0) {
+          for (int kb = 0; kb < pre; ++kb) {
+            const uint32_t k = it + kb, stage = k % kStages, phase = (k / kStages) & 1u;
+            ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, status);
+            if (!ok) break;
+            const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
+            ptx::mbar_arrive_expect_tx(full, stage_tx);
+            ptx::tma_load_2d(ring + stage * kStageBytes, tmJ, NMFA_KSLICE(kb) * kBK, b * kBM, full);
+            pending = kb + 1;
+          }
         }
-        it += pending;
-        pending = 0;
-        for (int kb = pre; kb < KB && ok; ++kb) {
-          const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
-          ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, a.status);
-          if (!ok) break;
-          const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
-          const uint32_t sA = ring + stage * Cfg::kStageBytes;
-          ptx::mbar_arrive_expect_tx(full, Cfg::kStageBytes);
-          ptx::tma_load_2d(sA, &tmJ, kslice(kb) * kBK, b * kBM, full);
-          ptx::tma_load_2d(sA + Cfg::kABytes, &tmS, kslice(kb) * kBK, sy, full);
-          ++it;
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        ok = wait_group_flags(gflags, nb, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
+                              t == 0 ? kStartTimeoutNs : kTimeoutNs);
+        // each lane acquired its own row blocks' counters; the warp barrier orders
+        // those acquires before lane 0's copies (memory ordering within the warp)
+        __syncwarp();
+        if (lane == 0) {
+          if (ok) ptx::fence_proxy_async_global();
+          // the S halves of the claimed slots (also on abort, so that their barriers complete)
+          for (int kb = 0; kb < pending; ++kb) {
+            const uint32_t k = it + kb, stage = k % kStages;
+            ptx::tma_load_2d(ring + stage * kStageBytes + kABytes, tmS, NMFA_KSLICE(kb) * kBK, sy,
+                             ptx::smem_u32(&ctl.full[stage]));
+          }
+          it += pending;
+          pending = 0;
+          for (int kb = pre; kb < KB_cur && ok; ++kb) {
+            const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
+            ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, status);
+            if (!ok) break;
+            const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
+            const uint32_t sA = ring + stage * kStageBytes;
+            ptx::mbar_arrive_expect_tx(full, stage_tx);
+            ptx::tma_load_2d(sA, tmJ, NMFA_KSLICE(kb) * kBK, b * kBM, full);
+            ptx::tma_load_2d(sA + kABytes, tmS, NMFA_KSLICE(kb) * kBK, sy, full);
+            ++it;
+          }
         }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     }
     if (!ok && lane == 0) {
       // J-only slots claimed before a failed wait get their S copy so their barriers complete
       for (int kb = 0; kb < pending; ++kb) {
         const uint32_t k = it + kb, stage = k % kStages;
-        ptx::tma_load_2d(ring + stage * Cfg::kStageBytes + Cfg::kABytes, &tmS, kslice(kb) * kBK, c * BN,
+        ptx::tma_load_2d(ring + stage * kStageBytes + kABytes, tmS_cur, NMFA_KSLICE(kb) * kBK, 0,
                          ptx::smem_u32(&ctl.full[stage]));
       }
       it += pending;
@@ -250,37 +416,42 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
         }
       }
     }
+#undef NMFA_KSLICE
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(kBM, BN);
-      uint32_t it = 0;
+      uint32_t it = 0, gstep = 0;
       bool ok = true;
       bool issued = false;
-      for (int t = 0; t < a.t_f && ok; ++t) {
-        if (t > 0) {
-          ok = wait_bar(ptx::smem_u32(&ctl.acc_empty), static_cast<uint32_t>((t - 1) & 1), &ctl, a.status);
-          if (!ok) break;
-        }
-        ptx::tc_fence_after();
-        for (int kb = 0; kb < KB; ++kb) {
-          const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
-          ok = wait_bar(ptx::smem_u32(&ctl.full[stage]), phase, &ctl, a.status);
-          if (!ok) break;
-          ptx::tc_fence_after();
-          const uint32_t sA = ring + stage * Cfg::kStageBytes;
-          const uint32_t sB = sA + Cfg::kABytes;
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            ptx::mma_bf16(tmem, ptx::sw128_desc(sA + kk * 32), ptx::sw128_desc(sB + kk * 32), idesc,
-                          (kb | kk) != 0 ? 1u : 0u);
+      for (int w = w_begin; w < w_end && ok; ++w) {
+        const TcGroup* g = groups + items[w].group;
+        const int KB = g->n_pad / kBK, t_f = g->t_f;
+        const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
+        for (int t = 0; t < t_f && ok; ++t, ++gstep) {
+          if (gstep > 0) {
+            ok = wait_bar(ptx::smem_u32(&ctl.acc_empty), (gstep - 1) & 1u, &ctl, status);
+            if (!ok) break;
           }
-          issued = true;
-          ptx::mma_commit(ptx::smem_u32(&ctl.empty[stage]));
-          ++it;
+          ptx::tc_fence_after();
+          for (int kb = 0; kb < KB; ++kb) {
+            const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
+            ok = wait_bar(ptx::smem_u32(&ctl.full[stage]), phase, &ctl, status);
+            if (!ok) break;
+            ptx::tc_fence_after();
+            const uint32_t sA = ring + stage * kStageBytes;
+            const uint32_t sB = sA + kABytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              ptx::mma_bf16(tmem, ptx::sw128_desc(sA + kk * 32), ptx::sw128_desc(sB + kk * 32), idesc,
+                            (kb | kk) != 0 ? 1u : 0u);
+            }
+            issued = true;
+            ptx::mma_commit(ptx::smem_u32(&ctl.empty[stage]));
+            ++it;
+          }
+          if (!ok) break;
+          ptx::mma_commit(ptx::smem_u32(&ctl.acc_full));
         }
-        if (!ok) break;
-        ptx::mma_commit(ptx::smem_u32(&ctl.acc_full));
       }
       if (!ok && issued) {
         // drain: wait (bounded) for every MMA issued so far
@@ -292,133 +463,13 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // Warp e serves TMEM lane quarter q = warp % 4 (spins 32q..32q+31 of the tile)
-    // and column group e / 4 (BN/4 replicas), 16 columns per tcgen05.ld.
-    constexpr int kCW = BN / 4;
     const int e = warp - 2;
-    const int q = warp & 3;
-    const int col0 = (e >> 2) * kCW;
-    const int i = b * kBM + q * 32 + lane;
-    const bool valid = i < a.n;
-    const float inv_d = a.inv_d32[i];
-    const float hi = a.h32[i];
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    const int rbase = c * BN + col0;
-    const size_t plane = static_cast<size_t>(a.r_pad) * a.n_pad;
-    const RoundKeys rk = make_round_keys(a.key);
-    uint32_t v[16], m[16];
-
-    // initial state (line 2, or the given s0) -> master in TMEM and BF16 buffer 0
-    for (int cc = 0; cc < kCW; cc += 16) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int r = rbase + cc + k;
-        float s = 0.0f;
-        if (a.s0 != nullptr && valid && r < a.replicas) s = static_cast<float>(a.s0[static_cast<int64_t>(r) * a.n + i]);
-        m[k] = __float_as_uint(s);
-        a.S16[static_cast<size_t>(r) * a.n_pad + i] = __float2bfloat16_rn(s);
-      }
-      ptx::tmem_st16(lane_base + BN + col0 + cc, m);
-    }
-    ptx::tmem_wait_st();
-    ptx::fence_proxy_async_global();
-    // All epilogue warps meet on an mbarrier (release/acquire within the CTA) with a
-    // bounded wait, so that a warp leaving on a timeout cannot strand the others.
-    const uint32_t epi_bar = ptx::smem_u32(&ctl.epi_sync);
-    auto epi_meet = [&](uint32_t phase) -> bool {
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(epi_bar);
-      const bool got = wait_bar(epi_bar, phase & 1u, &ctl, a.status);
-      return __all_sync(0xffffffffu, got);
-    };
-    bool ok = epi_meet(0);
-    if (ok && e == 0 && lane == 0) ptx::st_release_gpu(a.flags + static_cast<int64_t>(b) * a.rbk + c, 1u);
-
-    for (int t = 0; t < a.t_f && ok; ++t) {
-      float inv_T = 0.0f;
-      if (lane == 0) inv_T = 1.0f / static_cast<float>(a.T[t]);  // one FP64 load+convert per warp
-      inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
-      const bool write_phi = (t == a.t_f - 1) && a.phi_out != nullptr;
-      __nv_bfloat16* Snext = a.S16 + static_cast<size_t>((t + 1) & 1) * plane;
-      // (A) the step's Gaussian draws do not depend on the state: generate them while
-      // the tensor core computes this step's product, and park them in TMEM
-      for (int cc = 0; cc < kCW; cc += 16) {
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int r4 = rbase + cc + 4 * g;
-          const float4 z = gauss4_f32_fast(philox4x32_10_rk(
-              make_uint4(static_cast<uint32_t>(r4 >> 2), static_cast<uint32_t>(t), static_cast<uint32_t>(i), a.stream),
-              rk));
-          v[4 * g + 0] = __float_as_uint(a.sigma_ns * z.x);
-          v[4 * g + 1] = __float_as_uint(a.sigma_ns * z.y);
-          v[4 * g + 2] = __float_as_uint(a.sigma_ns * z.z);
-          v[4 * g + 3] = __float_as_uint(a.sigma_ns * z.w);
-        }
-        ptx::tmem_st16(lane_base + 2 * BN + col0 + cc, v);
-      }
-      ptx::tmem_wait_st();
-      // (B) the update, once the product is in TMEM
-      ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.acc_full), static_cast<uint32_t>(t & 1), &ctl, a.status));
-      if (!ok) break;
-      ptx::tc_fence_after();
-      for (int cc = 0; cc < kCW; cc += 16) {
-        uint32_t zn[16];
-        ptx::tmem_ld16(lane_base + col0 + cc, v);
-        ptx::tmem_ld16(lane_base + BN + col0 + cc, m);
-        ptx::tmem_ld16(lane_base + 2 * BN + col0 + cc, zn);
-        ptx::tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float P = __uint_as_float(v[k]) + hi;
-          const float phi = fmaf(P, inv_d, __uint_as_float(zn[k]));
-          const float sh = -ptx::tanh_approx(phi * inv_T);
-          const float s_new = fmaf(a.alpha, sh, a.one_m_alpha * __uint_as_float(m[k]));
-          m[k] = __float_as_uint(s_new);
-          v[k] = __float_as_uint(phi);
-        }
-        if (write_phi) {  // last step of a debug run only (warp-uniform branch)
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int r = rbase + cc + k;
-            if (valid && r < a.replicas)
-              a.phi_out[static_cast<int64_t>(r) * a.n + i] = static_cast<double>(__uint_as_float(v[k]));
-          }
-        }
-        ptx::tmem_st16(lane_base + BN + col0 + cc, m);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int r = rbase + cc + k;
-          Snext[static_cast<size_t>(r) * a.n_pad + i] =
-              valid ? __float2bfloat16_rn(__uint_as_float(m[k])) : __float2bfloat16_rn(0.0f);
-        }
-      }
-      ptx::tmem_wait_st();
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl.acc_empty));
-      ptx::fence_proxy_async_global();
-      ok = epi_meet(static_cast<uint32_t>(t + 1));
-      if (!ok) break;
-      // The release store publishes every epilogue thread's state writes: they
-      // happen before it through the rendezvous above (cumulativity).
-      if (e == 0 && lane == 0)
-        ptx::st_release_gpu(a.flags + static_cast<int64_t>(b) * a.rbk + c, static_cast<uint32_t>(t + 2));
-    }
-    // readout (lines 13-15): sign of the FP32 master state, zero reads as +1
-    if (__all_sync(0xffffffffu, ok && !aborted(&ctl))) {
-      for (int cc = 0; cc < kCW; cc += 16) {
-        ptx::tmem_ld16(lane_base + BN + col0 + cc, m);
-        ptx::tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int r = rbase + cc + k;
-          if (valid && r < a.replicas) {
-            const float s = __uint_as_float(m[k]);
-            a.signs[static_cast<int64_t>(r) * a.n + i] = s >= 0.0f ? int8_t(1) : int8_t(-1);
-            if (a.s_out != nullptr) a.s_out[static_cast<int64_t>(r) * a.n + i] = static_cast<double>(s);
-          }
-        }
-      }
+    uint32_t gstep = 0;
+    bool ok = true;
+    for (int w = w_begin; w < w_end && ok; ++w) {
+      const TcItem item = items[w];
+      const TcGroup* g = groups + item.group;
+      ok = epilogue_item<BN>(g, item.b, e, lane, tmem, &ctl, status, gstep);
     }
   }
 
@@ -426,8 +477,21 @@ nmfa_tc_kernel(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ 
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, Cfg::kTmemCols);
+    ptx::tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+// Copies a block of plan bytes (group descriptors, items, CTA offsets) from the
+// kernel's parameter space to device memory: no host-pinned buffer and no
+// allocation, so it can be recorded in a CUDA graph.
+constexpr int kUploadBytes = 30720;
+struct TcUpload {
+  uint32_t bytes;
+  uint32_t pad[3];
+  uint4 data[kUploadBytes / 16];
+};
+__global__ void tc_upload_kernel(const __grid_constant__ TcUpload u, uint4* dst) {
+  for (uint32_t k = threadIdx.x; k < u.bytes / 16; k += blockDim.x) dst[k] = u.data[k];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
@@ -459,93 +523,232 @@ int make_map_bf16(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols
   return NMFA_OK;
 }
 
-int pick_bn(int32_t replicas) { return replicas <= 64 ? 64 : 128; }
-
 template <int BN>
-int launch_tc_bn(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, cudaStream_t st) {
-  using Cfg = TcCfg<BN>;
-  const int nb = pb.n_pad / kBM;
-  const int r_pad = (rp.replicas + BN - 1) / BN * BN;
-  const int rbk = r_pad / BN;
-  __nv_bfloat16* S16 = static_cast<__nv_bfloat16*>(ws.S16);
-  const size_t s_bytes = 2ull * r_pad * pb.n_pad * 2;
-  uint32_t* flags = reinterpret_cast<uint32_t*>(static_cast<char*>(ws.S16) + s_bytes);
-  CUtensorMap tmJ, tmS;
-  int rc;
-  if ((rc = make_map_bf16(&tmJ, pb.Jq, pb.n_pad, pb.n_pad, kBM))) return rc;
-  if ((rc = make_map_bf16(&tmS, S16, 2ull * r_pad, pb.n_pad, BN))) return rc;
-  auto kern = nmfa_tc_kernel<BN>;
-  if ((rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(Cfg::kSmemBytes)),
-                       "tensor kernel attribute")))
-    return rc;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, Cfg::kSmemBytes),
-                       "occupancy")))
-    return rc;
-  const int capacity = per_sm * sms;
-  const int groups_per_wave = capacity / nb;
-  if (groups_per_wave < 1)
-    return set_error(NMFA_EUNSUPPORTED, "tensor path: n too large for one co-resident replica block");
-  if ((rc = cuda_error(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * nb * rbk, st), "flag reset"))) return rc;
-  TcArgs a{};
-  a.n = pb.n;
-  a.n_pad = pb.n_pad;
-  a.r_pad = r_pad;
-  a.replicas = rp.replicas;
-  a.t_f = rp.t_f;
-  a.rbk = rbk;
-  a.inv_d32 = pb.inv_d32;
-  a.h32 = pb.h32;
-  a.T = rp.T;
-  a.sigma_ns = static_cast<float>(rp.sigma * rp.noise_sign);
-  a.alpha = static_cast<float>(rp.alpha);
-  a.one_m_alpha = static_cast<float>(1.0 - rp.alpha);
-  a.key = make_noise_key(rp.seed);
-  a.stream = rp.stream_id;
-  a.s0 = rp.s0;
-  a.s_out = rp.s_out;
-  a.phi_out = rp.phi_out;
-  a.signs = rp.signs;
-  a.S16 = S16;
-  a.flags = flags;
-  a.status = ws.status;
-  for (int c0 = 0; c0 < rbk; c0 += groups_per_wave) {
-    a.c_offset = c0;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(nb, std::min(groups_per_wave, rbk - c0), 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = Cfg::kSmemBytes;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if ((rc = cuda_error(cudaLaunchKernelEx(&cfg, kern, tmJ, tmS, a), "tensor kernel launch"))) return rc;
-    count_launch();
+int co_resident_ctas_bn(int* capacity) {
+  static int cached = -1;
+  if (cached < 0) {
+    int rc;
+    if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(kSmemBytes)),
+                         "tensor kernel attribute")))
+      return rc;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN>,
+                                                                       TcShape<BN>::kThreads, kSmemBytes),
+                         "occupancy")))
+      return rc;
+    cached = per_sm * sms;
   }
+  *capacity = cached;
   return NMFA_OK;
 }
+int co_resident_ctas(int bn, int* capacity) {
+  return bn == 64 ? co_resident_ctas_bn<64>(capacity) : co_resident_ctas_bn<128>(capacity);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes) {
-  const int bn = pick_bn(replicas);
-  const int64_t r_pad = (replicas + bn - 1) / bn * bn;
-  const int64_t nb = pb.n_pad / kBM;
-  *bytes = 2 * r_pad * pb.n_pad * 2 + (nb * (r_pad / bn) * 4 + 255) / 256 * 256;
+int tc_pick_bn(int32_t replicas) { return replicas <= 64 ? 64 : 128; }
+
+// ---------------------------------------------------------------------------
+// Planning: every job (instance run) is split into groups of bn replicas; every
+// group needs nb = n_pad/128 co-resident CTAs for its whole run.  Groups are placed
+// on the persistent grid's CTA slots by list scheduling (longest first, on the nb
+// slots that free up earliest), so each CTA walks its items in start order and any
+// CTA waiting for a group's peers waits only on groups that started earlier: no
+// cycle of waits can form.
+// ---------------------------------------------------------------------------
+int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
+  if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
+  int capacity = 0;
+  int rc = co_resident_ctas(jobs[0].bn, &capacity);
+  if (rc) return rc;
+  size_t ngroups = 0, nitems = 0, flags = 0, state = 0;
+  for (int j = 0; j < count; ++j) {
+    const int bn = jobs[j].bn;
+    const int nb = jobs[j].pb.n_pad / kBM;
+    if (bn != jobs[0].bn) return set_error(NMFA_EINVAL, "one plan takes one tile width");
+    if (nb > capacity) return set_error(NMFA_EUNSUPPORTED, "tensor path: n too large for one co-resident replica block");
+    const int groups = (jobs[j].rp.replicas + bn - 1) / bn;
+    ngroups += groups;
+    nitems += static_cast<size_t>(groups) * nb;
+    flags += static_cast<size_t>(groups) * nb;
+    state += static_cast<size_t>(groups) * 2 * bn * jobs[j].pb.n_pad * 2;
+  }
+  *bytes = static_cast<int64_t>(align_up(ngroups * sizeof(TcGroup), 256) + align_up(nitems * sizeof(TcItem), 256) +
+                                align_up((static_cast<size_t>(capacity) + 1) * 4, 256) + align_up(flags * 4, 256) + state);
   return NMFA_OK;
 }
 
-int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, cudaStream_t st) {
-  if (pb.fp8) return set_error(NMFA_EUNSUPPORTED, "FP8-J tensor path is not available in this build");
-  if (pb.n_pad % kBM != 0) return set_error(NMFA_EINVAL, "tensor path: n_pad must be a multiple of 128");
-  return pick_bn(rp.replicas) == 64 ? launch_tc_bn<64>(pb, rp, ws, st) : launch_tc_bn<128>(pb, rp, ws, st);
+int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan) {
+  if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
+  int capacity = 0;
+  int rc = co_resident_ctas(jobs[0].bn, &capacity);
+  if (rc) return rc;
+  int64_t need = 0;
+  if ((rc = tc_plan_bytes(jobs, count, &need))) return rc;
+  if (need > ws_bytes) return set_error(NMFA_EINVAL, "tensor path: workspace too small");
+  struct G {
+    int job, c, nb;
+    double dur;
+  };
+  std::vector<G> gl;
+  size_t nitems = 0, nflags = 0;
+  for (int j = 0; j < count; ++j) {
+    const int bn = jobs[j].bn, nb = jobs[j].pb.n_pad / kBM;
+    const int groups = (jobs[j].rp.replicas + bn - 1) / bn;
+    for (int c = 0; c < groups; ++c) {
+      gl.push_back({j, c, nb, static_cast<double>(jobs[j].rp.t_f) * (2.0 * nb + 8.0)});
+      nitems += nb;
+      nflags += nb;
+    }
+  }
+  char* base = static_cast<char*>(ws);
+  const size_t off_items = align_up(gl.size() * sizeof(TcGroup), 256);
+  const size_t off_first = off_items + align_up(nitems * sizeof(TcItem), 256);
+  const size_t off_flags = off_first + align_up((static_cast<size_t>(capacity) + 1) * 4, 256);
+  const size_t off_state = off_flags + align_up(nflags * 4, 256);
+  // group descriptors
+  plan->host.assign(off_flags, 0);
+  TcGroup* hg = reinterpret_cast<TcGroup*>(plan->host.data());
+  size_t flag_pos = 0, state_pos = off_state;
+  std::vector<uint32_t*> gflags(gl.size());
+  for (size_t k = 0; k < gl.size(); ++k) {
+    const TcJob& jb = jobs[gl[k].job];
+    TcGroup& g = hg[k];
+    const int bn = jb.bn;
+    g.n = jb.pb.n;
+    g.n_pad = jb.pb.n_pad;
+    g.bn = bn;
+    g.replicas = jb.rp.replicas;
+    g.r0 = gl[k].c * bn;
+    g.t_f = jb.rp.t_f;
+    g.inv_d32 = jb.pb.inv_d32;
+    g.h32 = jb.pb.h32;
+    g.T = jb.rp.T;
+    g.s0 = jb.rp.s0;
+    g.s_out = jb.rp.s_out;
+    g.phi_out = jb.rp.phi_out;
+    g.signs = jb.rp.signs;
+    g.sigma_ns = static_cast<float>(jb.rp.sigma * jb.rp.noise_sign);
+    g.alpha = static_cast<float>(jb.rp.alpha);
+    g.one_m_alpha = static_cast<float>(1.0 - jb.rp.alpha);
+    g.seed_lo = static_cast<uint32_t>(jb.rp.seed);
+    g.seed_hi = static_cast<uint32_t>(jb.rp.seed >> 32);
+    g.stream = jb.rp.stream_id;
+    g.flags = reinterpret_cast<uint32_t*>(base + off_flags) + flag_pos;
+    flag_pos += gl[k].nb;
+    g.S16 = reinterpret_cast<__nv_bfloat16*>(base + state_pos);
+    state_pos += static_cast<size_t>(2) * bn * g.n_pad * 2;
+    if ((rc = make_map_bf16(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad, kBM))) return rc;
+    if ((rc = make_map_bf16(&g.tmS, g.S16, 2ull * bn, g.n_pad, bn))) return rc;
+  }
+  // list scheduling of groups onto CTA slots
+  std::vector<int> order(gl.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return gl[x].dur > gl[y].dur; });
+  std::vector<double> free_at(capacity, 0.0);
+  std::vector<std::vector<TcItem>> per_cta(capacity);
+  std::vector<int> slots(capacity);
+  for (int gi : order) {
+    for (int s = 0; s < capacity; ++s) slots[s] = s;
+    std::stable_sort(slots.begin(), slots.end(), [&](int x, int y) { return free_at[x] < free_at[y]; });
+    const int nb = gl[gi].nb;
+    double start = 0.0;
+    for (int b = 0; b < nb; ++b) start = std::max(start, free_at[slots[b]]);
+    for (int b = 0; b < nb; ++b) {
+      per_cta[slots[b]].push_back(TcItem{gi, b});
+      free_at[slots[b]] = start + gl[gi].dur;
+    }
+  }
+  int grid = 0;
+  for (int s = 0; s < capacity; ++s)
+    if (!per_cta[s].empty()) grid = s + 1;
+  TcItem* hi = reinterpret_cast<TcItem*>(plan->host.data() + off_items);
+  int32_t* hf = reinterpret_cast<int32_t*>(plan->host.data() + off_first);
+  int32_t pos = 0;
+  for (int s = 0; s < grid; ++s) {
+    hf[s] = pos;
+    for (const TcItem& it : per_cta[s]) hi[pos++] = it;
+  }
+  hf[grid] = pos;
+  plan->dev = base;
+  plan->groups_off = 0;
+  plan->items_off = off_items;
+  plan->first_off = off_first;
+  plan->flags_off = off_flags;
+  plan->flags_bytes = nflags * 4;
+  plan->grid = grid;
+  plan->bn = jobs[0].bn;
+  plan->status = status;
+  plan->makespan = *std::max_element(free_at.begin(), free_at.end());
+  return NMFA_OK;
 }
 
+// Enqueue: upload the plan (from kernel parameters), clear the epoch counters,
+// launch the persistent kernel.  Everything is stream-ordered and capturable.
+int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
+  int rc;
+  if (upload) {
+    const size_t total = plan.flags_off;  // descriptors, items and offsets precede the flags
+    TcUpload u;
+    for (size_t off = 0; off < total; off += kUploadBytes) {
+      const size_t chunk = std::min<size_t>(kUploadBytes, total - off);
+      u.bytes = static_cast<uint32_t>(chunk);
+      std::memcpy(u.data, plan.host.data() + off, chunk);
+      tc_upload_kernel<<<1, 256, 0, st>>>(u, reinterpret_cast<uint4*>(static_cast<char*>(plan.dev) + off));
+      count_launch();
+      if ((rc = cuda_error(cudaGetLastError(), "plan upload"))) return rc;
+    }
+  }
+  if ((rc = cuda_error(cudaMemsetAsync(static_cast<char*>(plan.dev) + plan.flags_off, 0, plan.flags_bytes, st),
+                       "flag reset")))
+    return rc;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(plan.grid, 1, 1);
+  cfg.blockDim = dim3(plan.bn == 64 ? TcShape<64>::kThreads : TcShape<128>::kThreads, 1, 1);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const char* d = static_cast<const char*>(plan.dev);
+  const TcGroup* dg = reinterpret_cast<const TcGroup*>(d + plan.groups_off);
+  const TcItem* di = reinterpret_cast<const TcItem*>(d + plan.items_off);
+  const int32_t* df = reinterpret_cast<const int32_t*>(d + plan.first_off);
+  const cudaError_t ce = plan.bn == 64 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
+                                       : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128>, dg, di, df, plan.status);
+  if ((rc = cuda_error(ce, "tensor kernel launch"))) return rc;
+  count_launch();
+  return NMFA_OK;
+}
+
+int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes) {
+  TcJob jb{};
+  jb.pb = pb;
+  jb.rp.replicas = replicas;
+  jb.bn = tc_pick_bn(replicas);
+  return tc_plan_bytes(&jb, 1, bytes);
+}
+
+int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, cudaStream_t st) {
+  if (pb.fp8) return set_error(NMFA_EINVAL, "tensor kernel takes BF16 couplings (expand FP8 storage first)");
+  if (pb.n_pad % kBM != 0) return set_error(NMFA_EINVAL, "tensor path: n_pad must be a multiple of 128");
+  TcJob jb{};
+  jb.pb = pb;
+  jb.rp = rp;
+  jb.bn = tc_pick_bn(rp.replicas);
+  TcPlan plan;
+  int rc = tc_build_plan(&jb, 1, ws.S16, ws.bytes, ws.status, &plan);
+  if (rc) return rc;
+  return tc_enqueue_plan(plan, true, st);
+}
 
 // ----------------------------------------------------------------------------
 // Scratch without allocation, for nmfa_run_device_noalloc.

@@ -217,6 +217,8 @@ void free_problem(nmfa_problem* p) {
 
 }  // namespace
 
+static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas);
+
 extern "C" {
 
 const char* nmfa_last_error(void) { return t_last_error.c_str(); }
@@ -494,14 +496,20 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
       pb.n = p->n;
       pb.n_pad = p->n_pad;
       pb.Jq = p->Jq;
-      pb.fp8 = p->precision == NMFA_BF16_FP8J;
+      pb.fp8 = false;
       pb.inv_d32 = p->inv_d32;
       pb.h32 = p->h32;
       int64_t bytes = 0;
       if ((rc = tc_workspace_bytes(pb, replicas, &bytes))) return rc;
-      if ((rc = ensure_buf(p->ws, static_cast<size_t>(bytes)))) return rc;
+      // FP8-stored couplings are expanded to BF16 in front of the kernel's scratch
+      const size_t jexp = p->precision == NMFA_BF16_FP8J ? static_cast<size_t>(p->n_pad) * p->n_pad * 2 : 0;
+      if ((rc = ensure_buf(p->ws, jexp + static_cast<size_t>(bytes)))) return rc;
+      if (jexp) {
+        if ((rc = launch_expand_e4m3_bf16(p->Jq, p->ws.p, static_cast<int64_t>(p->n_pad) * p->n_pad, st))) return rc;
+        pb.Jq = p->ws.p;
+      }
       TcWorkspace ws{};
-      ws.S16 = p->ws.p;
+      ws.S16 = static_cast<char*>(p->ws.p) + jexp;
       ws.bytes = bytes;
       ws.status = p->status;
       rc = launch_tc(pb, rp, ws, st);
@@ -643,6 +651,237 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
   return cuda_error(cudaEventRecord(p->done, st), "event record");
 }
 
+// ---------------------------------------------------------------------------
+// Batches: many tensor-path runs (different instances, sizes, replica counts,
+// schedules) in one persistent launch.
+// ---------------------------------------------------------------------------
+struct nmfa_batch {
+  std::vector<nmfa_problem*> problems;
+  std::vector<nmfa_job> jobs;
+  std::vector<int> bn;
+  std::vector<DevBuf> ws;   // one workspace per plan
+  DevBuf jexp;              // BF16 expansions of FP8-stored couplings
+  std::vector<std::pair<int, size_t>> expand;  // (job, offset into jexp)
+  DevBuf signs;             // sign scratch for jobs that did not supply a buffer
+  std::vector<int8_t*> signs_ptr;
+  int32_t* status = nullptr;
+  std::vector<TcPlan> plans;  // one persistent launch per tile width in the batch
+  cudaStream_t own = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+  std::mutex mu;
+};
+
+static void free_batch(nmfa_batch* b) {
+  if (b == nullptr) return;
+  if (b->done) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (DevBuf& w : b->ws)
+    if (w.p) cudaFree(w.p);
+  if (b->signs.p) cudaFree(b->signs.p);
+  if (b->jexp.p) cudaFree(b->jexp.p);
+  if (b->status) cudaFree(b->status);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->own) cudaStreamDestroy(b->own);
+  delete b;
+}
+
+// Enqueues the batch's work (flag reset, the persistent kernel, one energy kernel
+// per job) on `st`; the plan was uploaded at creation.
+static int batch_enqueue(nmfa_batch* b, cudaStream_t st) {
+  int rc;
+  for (const auto& ex : b->expand) {
+    const nmfa_problem* p = b->problems[ex.first];
+    if ((rc = launch_expand_e4m3_bf16(p->Jq, static_cast<char*>(b->jexp.p) + ex.second,
+                                      static_cast<int64_t>(p->n_pad) * p->n_pad, st)))
+      return rc;
+  }
+  for (const TcPlan& plan : b->plans)
+    if ((rc = tc_enqueue_plan(plan, false, st))) return rc;
+  for (size_t j = 0; j < b->jobs.size(); ++j) {
+    const nmfa_job& jb = b->jobs[j];
+    if (jb.energy_dev == nullptr && jb.energy_i64_dev == nullptr) continue;
+    nmfa_problem* p = b->problems[j];
+    EnergyProblem ep{};
+    ep.n = p->n;
+    ep.J8 = p->J8;
+    ep.J64 = p->J64;
+    ep.h = p->h64;
+    ep.integer_valued = p->integer_valued;
+    if ((rc = launch_energy(ep, b->signs_ptr[j], jb.replicas, jb.energy_dev, jb.energy_i64_dev, st))) return rc;
+  }
+  return NMFA_OK;
+}
+
+int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32_t count, int32_t options,
+                      nmfa_batch** out) {
+  if (out == nullptr) return set_error(NMFA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || problems == nullptr || jobs == nullptr) return set_error(NMFA_EINVAL, "empty batch");
+  for (int32_t j = 0; j < count; ++j) {
+    const nmfa_problem* p = problems[j];
+    const nmfa_job& jb = jobs[j];
+    if (p == nullptr) return set_error(NMFA_EINVAL, "NULL problem in batch");
+    if (p->precision != NMFA_BF16 && p->precision != NMFA_BF16_FP8J)
+      return set_error(NMFA_EUNSUPPORTED, "batches take NMFA_BF16 or NMFA_BF16_FP8J problems");
+    if (jb.t_f < 0 || (jb.t_f > 0 && jb.T_dev == nullptr)) return set_error(NMFA_EINVAL, "bad t_f or T in batch");
+    if (!(jb.sigma >= 0.0) || !(jb.alpha > 0.0 && jb.alpha <= 1.0) || jb.replicas < 1)
+      return set_error(NMFA_EINVAL, "bad sigma, alpha or replicas in batch");
+    if (jb.energy_i64_dev != nullptr && !p->integer_valued)
+      return set_error(NMFA_EINVAL, "integer energies requested for a real-valued problem");
+    if (p->device != problems[0]->device) return set_error(NMFA_EINVAL, "batch problems live on different devices");
+  }
+  nmfa_batch* b = new nmfa_batch();
+  auto fail = [&](int code) {
+    std::string msg = t_last_error;
+    free_batch(b);
+    t_last_error = msg;
+    return code;
+  };
+  b->problems.assign(problems, problems + count);
+  b->jobs.assign(jobs, jobs + count);
+  b->device = problems[0]->device;
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(b->device), "cudaSetDevice"))) return fail(rc);
+  if ((rc = cuda_error(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), "stream"))) return fail(rc);
+  if ((rc = cuda_error(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event"))) return fail(rc);
+  if ((rc = cuda_error(cudaMalloc(&b->status, 4), "status"))) return fail(rc);
+  if ((rc = cuda_error(cudaMemset(b->status, 0, 4), "status"))) return fail(rc);
+  size_t sign_bytes = 0;
+  for (int32_t j = 0; j < count; ++j)
+    if (jobs[j].signs_dev == nullptr) sign_bytes += static_cast<size_t>(jobs[j].replicas) * problems[j]->n;
+  if (sign_bytes && (rc = ensure_buf(b->signs, sign_bytes))) return fail(rc);
+  size_t jexp_bytes = 0;
+  for (int32_t j = 0; j < count; ++j)
+    if (problems[j]->precision == NMFA_BF16_FP8J) {
+      b->expand.emplace_back(j, jexp_bytes);
+      jexp_bytes += (static_cast<size_t>(problems[j]->n_pad) * problems[j]->n_pad * 2 + 255) / 256 * 256;
+    }
+  if (jexp_bytes && (rc = ensure_buf(b->jexp, jexp_bytes))) return fail(rc);
+  std::vector<TcJob> tj(count);
+  size_t sp = 0;
+  b->signs_ptr.resize(count);
+  for (int32_t j = 0; j < count; ++j) {
+    nmfa_problem* p = problems[j];
+    const nmfa_job& jb = jobs[j];
+    int8_t* sg = jb.signs_dev;
+    if (sg == nullptr) {
+      sg = static_cast<int8_t*>(b->signs.p) + sp;
+      sp += static_cast<size_t>(jb.replicas) * p->n;
+    }
+    b->signs_ptr[j] = sg;
+    TcJob& t = tj[j];
+    t.pb.n = p->n;
+    t.pb.n_pad = p->n_pad;
+    t.pb.Jq = p->Jq;
+    for (const auto& ex : b->expand)
+      if (ex.first == j) t.pb.Jq = static_cast<char*>(b->jexp.p) + ex.second;
+    t.pb.fp8 = false;
+    t.pb.inv_d32 = p->inv_d32;
+    t.pb.h32 = p->h32;
+    t.rp = RunParams{};
+    t.rp.T = jb.T_dev;
+    t.rp.t_f = jb.t_f;
+    t.rp.sigma = jb.sigma;
+    t.rp.alpha = jb.alpha;
+    t.rp.replicas = jb.replicas;
+    t.rp.seed = jb.seed;
+    t.rp.stream_id = jb.stream_id;
+    t.rp.noise_sign = 1;
+    t.rp.signs = sg;
+    t.bn = (options & NMFA_BATCH_BN64) ? 64
+           : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
+                                             : tc_pick_bn(jb.replicas);
+    b->bn.push_back(t.bn);
+  }
+  for (int bnv : {128, 64}) {
+    std::vector<TcJob> part;
+    for (const TcJob& t : tj)
+      if (t.bn == bnv) part.push_back(t);
+    if (part.empty()) continue;
+    int64_t bytes = 0;
+    if ((rc = tc_plan_bytes(part.data(), static_cast<int32_t>(part.size()), &bytes))) return fail(rc);
+    b->ws.emplace_back();
+    if ((rc = ensure_buf(b->ws.back(), static_cast<size_t>(bytes)))) return fail(rc);
+    b->plans.emplace_back();
+    if ((rc = tc_build_plan(part.data(), static_cast<int32_t>(part.size()), b->ws.back().p, bytes, b->status,
+                            &b->plans.back())))
+      return fail(rc);
+    // upload the plan once (kernel-parameter copies on the batch's stream)
+    if ((rc = tc_enqueue_plan(b->plans.back(), true, b->own))) return fail(rc);
+  }
+  if ((rc = cuda_error(cudaStreamSynchronize(b->own), "batch warm-up"))) return fail(rc);
+  if (options & NMFA_BATCH_GRAPH) {
+    if ((rc = cuda_error(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "capture"))) return fail(rc);
+    rc = batch_enqueue(b, b->own);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->own, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return fail(rc);
+    }
+    if ((rc = cuda_error(ce, "end capture"))) return fail(rc);
+    b->graph = g;
+    if ((rc = cuda_error(cudaGraphInstantiate(&b->exec, g, 0), "graph instantiate"))) return fail(rc);
+  }
+  *out = b;
+  return NMFA_OK;
+}
+
+int nmfa_batch_launch(nmfa_batch* b, void* cuda_stream) {
+  if (b == nullptr) return set_error(NMFA_EINVAL, "NULL batch");
+  std::lock_guard<std::mutex> g(b->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(b->device), "cudaSetDevice"))) return rc;
+  if ((rc = cuda_error(cudaStreamWaitEvent(st, b->done, 0), "stream wait"))) return rc;
+  if (b->exec != nullptr) {
+    if ((rc = cuda_error(cudaGraphLaunch(b->exec, st), "graph launch"))) return rc;
+    count_launch(1);
+  } else if ((rc = batch_enqueue(b, st))) {
+    return rc;
+  }
+  return cuda_error(cudaEventRecord(b->done, st), "event record");
+}
+
+int nmfa_batch_sync(nmfa_batch* b) {
+  if (b == nullptr) return set_error(NMFA_EINVAL, "NULL batch");
+  int rc = cuda_error(cudaEventSynchronize(b->done), "sync");
+  if (rc) return rc;
+  int32_t st = 0;
+  if ((rc = cuda_error(cudaMemcpy(&st, b->status, 4, cudaMemcpyDeviceToHost), "status read"))) return rc;
+  if (st != kStatusOk) {
+    cudaMemset(b->status, 0, 4);
+    return set_error(NMFA_ETIMEOUT, "a bounded device-side wait gave up");
+  }
+  return NMFA_OK;
+}
+
+int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes) {
+  if (b == nullptr) return set_error(NMFA_EINVAL, "NULL batch");
+  if (grid) {
+    int32_t gmax = 0;
+    for (const TcPlan& pl : b->plans) gmax = std::max<int32_t>(gmax, pl.grid);
+    *grid = gmax;
+  }
+  if (groups) {
+    int32_t g = 0;
+    for (size_t j = 0; j < b->jobs.size(); ++j) g += (b->jobs[j].replicas + b->bn[j] - 1) / b->bn[j];
+    *groups = g;
+  }
+  if (workspace_bytes) {
+    size_t tot = b->signs.bytes;
+    for (const DevBuf& w : b->ws) tot += w.bytes;
+    *workspace_bytes = static_cast<int64_t>(tot);
+  }
+  return NMFA_OK;
+}
+
+void nmfa_batch_destroy(nmfa_batch* b) { free_batch(b); }
+
 // Tuning hook for the CUDA-core paths (replicas per CTA: 0 = automatic, else 1/2/4/8).
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
   if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
@@ -652,3 +891,91 @@ int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: replicas per tile (bn = 64 or 128) for the tensor path, chosen by
+// timing a short run of each candidate on the problem itself and cached by the
+// run's shape (n_pad, replicas) only, so that an instance's tiling (and hence
+// its results) never depends on what else shares a batch.  Results are identical
+// for either choice; the tuner only trades tile count against tile width.
+// ---------------------------------------------------------------------------
+#include <map>
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tune_cache;
+
+static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas) {
+  if (replicas <= 64 || p->precision != NMFA_BF16) return tc_pick_bn(replicas);
+  const std::pair<int, int> key(p->n_pad, replicas);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+  }
+  int best = tc_pick_bn(replicas);
+  float best_ms = 1e30f;
+  const int t_f = 24;
+  double* T = nullptr;
+  int8_t* signs = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DevBuf ws;
+  bool okc = cudaMalloc(&T, sizeof(double) * t_f) == cudaSuccess &&
+             cudaMalloc(&signs, static_cast<size_t>(replicas) * p->n) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (okc) {
+    std::vector<double> Th(t_f, 1.0);
+    okc = cudaMemcpy(T, Th.data(), sizeof(double) * t_f, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  for (int bn : {64, 128}) {
+    if (!okc) break;
+    TcJob jb{};
+    jb.pb.n = p->n;
+    jb.pb.n_pad = p->n_pad;
+    jb.pb.Jq = p->Jq;
+    jb.pb.inv_d32 = p->inv_d32;
+    jb.pb.h32 = p->h32;
+    jb.rp.T = T;
+    jb.rp.t_f = t_f;
+    jb.rp.sigma = 0.15;
+    jb.rp.alpha = 0.15;
+    jb.rp.replicas = replicas;
+    jb.rp.noise_sign = 1;
+    jb.rp.signs = signs;
+    jb.bn = bn;
+    int64_t bytes = 0;
+    TcPlan plan;
+    if (tc_plan_bytes(&jb, 1, &bytes) || ensure_buf(ws, static_cast<size_t>(bytes)) ||
+        tc_build_plan(&jb, 1, ws.p, bytes, p->status, &plan))
+      continue;
+    float ms = 0.0f;
+    bool good = tc_enqueue_plan(plan, true, st) == NMFA_OK && cudaStreamSynchronize(st) == cudaSuccess;
+    for (int rep = 0; rep < 2 && good; ++rep) {
+      good = cudaEventRecord(e0, st) == cudaSuccess && tc_enqueue_plan(plan, true, st) == NMFA_OK &&
+             cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    if (good && ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  if (ws.p) cudaFree(ws.p);
+  if (T) cudaFree(T);
+  if (signs) cudaFree(signs);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache[key] = best;
+  return best;
+}
+
+extern "C" int nmfa_autotune_bn(nmfa_problem* p, int32_t replicas, int32_t* bn) {
+  if (p == nullptr || bn == nullptr || replicas < 1) return set_error(NMFA_EINVAL, "bad autotune arguments");
+  if (p->precision != NMFA_BF16) return set_error(NMFA_EUNSUPPORTED, "autotuning is for NMFA_BF16 problems");
+  std::lock_guard<std::mutex> g(p->mu);
+  *bn = nmfa_autotuned_bn(p, replicas);
+  return NMFA_OK;
+}

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "nmfa.h"
 
@@ -93,6 +94,8 @@ int launch_row_norms_csr(int32_t n, const int32_t* row_ptr, const double* val64,
 int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int64_t rows,
                          int64_t ld, cudaStream_t st);
 int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st);
+// Stored E4M3 couplings -> BF16 copy for the tensor kernel (count a multiple of 16).
+int launch_expand_e4m3_bf16(const void* src, void* dst, int64_t count, cudaStream_t st);
 
 // ---- tcgen05 tensor path ------------------------------------------------------
 struct TcProblem {
@@ -110,6 +113,25 @@ struct TcWorkspace {
   int64_t bytes;
 };
 int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes);
+// One instance run on the tensor path, and a launch plan for a batch of them.
+struct TcJob {
+  TcProblem pb;
+  RunParams rp;
+  int bn;                  // replicas per tile: 64 or 128
+};
+struct TcPlan {
+  std::vector<unsigned char> host;   // group descriptors, items, per-CTA offsets
+  void* dev = nullptr;               // workspace base
+  size_t groups_off = 0, items_off = 0, first_off = 0, flags_off = 0, flags_bytes = 0;
+  int grid = 0;
+  int bn = 128;
+  int32_t* status = nullptr;
+  double makespan = 0.0;             // scheduler's estimate (relative units)
+};
+int tc_pick_bn(int32_t replicas);
+int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
+int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan);
+int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st);
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,
               cudaStream_t st);
 // Same launch with the scratch taken from a fixed-size static device array.

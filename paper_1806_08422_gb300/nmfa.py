@@ -41,6 +41,12 @@ SIGNATURES = {
     "nmfa_run_device": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _P, _P, _P, _P]),
     "nmfa_run_device_noalloc": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _P, _P, _P, _P]),
     "nmfa_sync": (ctypes.c_int, [_P]),
+    "nmfa_batch_create": (ctypes.c_int, [_P, _P, _i32, _i32, ctypes.POINTER(_P)]),
+    "nmfa_batch_launch": (ctypes.c_int, [_P, _P]),
+    "nmfa_batch_sync": (ctypes.c_int, [_P]),
+    "nmfa_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nmfa_batch_destroy": (None, [_P]),
+    "nmfa_autotune_bn": (ctypes.c_int, [_P, _i32, _P]),
     "nmfa_debug_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _i32, _P, _P, _P, _P, _P,
                                       _P, _P]),
     "nmfa_problem_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -191,6 +197,58 @@ def nmfa_last_error():
 
 def nmfa_version():
     return load().nmfa_version().decode()
+
+
+class nmfa_job(ctypes.Structure):
+    _fields_ = [("T_dev", ctypes.c_void_p), ("t_f", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("replicas", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("stream_id", ctypes.c_uint32), ("signs_dev", ctypes.c_void_p), ("energy_dev", ctypes.c_void_p),
+                ("energy_i64_dev", ctypes.c_void_p)]
+
+
+NMFA_BATCH_GRAPH = 1
+NMFA_BATCH_AUTOTUNE = 2
+NMFA_BATCH_BN64 = 4
+
+
+def make_job(T_dev, sigma, alpha, replicas, seed=0, stream_id=0, signs=None, energy=None, energy_i64=None):
+    return nmfa_job(T_dev.data_ptr(), int(T_dev.numel()), float(sigma), float(alpha), int(replicas), int(seed),
+                    int(stream_id), None if signs is None else signs.data_ptr(),
+                    None if energy is None else energy.data_ptr(),
+                    None if energy_i64 is None else energy_i64.data_ptr())
+
+
+def nmfa_batch_create(handles, jobs, options=0):
+    n = len(handles)
+    harr = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    jarr = (nmfa_job * n)(*jobs)
+    out = ctypes.c_void_p()
+    _check(load().nmfa_batch_create(harr, jarr, n, int(options), ctypes.byref(out)))
+    return out
+
+
+def nmfa_batch_launch(batch, stream=None):
+    _check(load().nmfa_batch_launch(batch, _stream_ptr(stream)))
+
+
+def nmfa_batch_sync(batch):
+    _check(load().nmfa_batch_sync(batch))
+
+
+def nmfa_batch_info(batch):
+    g, n, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().nmfa_batch_info(batch, ctypes.byref(g), ctypes.byref(n), ctypes.byref(b)))
+    return {"grid": g.value, "groups": n.value, "workspace_bytes": b.value}
+
+
+def nmfa_batch_destroy(batch):
+    load().nmfa_batch_destroy(batch)
+
+
+def nmfa_autotune_bn(handle, replicas):
+    bn = ctypes.c_int32()
+    _check(load().nmfa_autotune_bn(handle, int(replicas), ctypes.byref(bn)))
+    return bn.value
 
 
 # ---------------------------------------------------------------- convenience

@@ -1,0 +1,153 @@
+"""Ragged batches on the tensor path: many instances (different sizes, replica
+counts, schedules and noise streams) in one persistent launch, optionally replayed
+from a CUDA graph.  Every instance's result must be bit-identical to running it
+alone (batching invariance), and its Eq. (1) energies exact against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_08422_gb300 import instances as inst
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    import torch
+    return torch, torch.device("cuda", 0)
+
+
+def _alone(p, T_dev, R, seed, stream_id):
+    torch, dev = _dev()
+    s = torch.empty((R, p.n), dtype=torch.int8, device=dev)
+    e = torch.empty(R, dtype=torch.int64, device=dev)
+    p.run_device(T_dev, 0.15, 0.15, R, seed=seed, stream_id=stream_id, signs=s, energy_i64=e)
+    p.sync()
+    return s.cpu().numpy(), e.cpu().numpy()
+
+
+def _batch(problems, specs, options):
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    outs, jobs = [], []
+    for p, (T_dev, R, seed, sid) in zip(problems, specs):
+        s = torch.empty((R, p.n), dtype=torch.int8, device=dev)
+        e = torch.empty(R, dtype=torch.int64, device=dev)
+        outs.append((s, e))
+        jobs.append(nmfa.make_job(T_dev, 0.15, 0.15, R, seed=seed, stream_id=sid, signs=s, energy_i64=e))
+    b = nmfa.nmfa_batch_create([p.handle for p in problems], jobs, options)
+    return b, outs
+
+
+@pytest.mark.parametrize("options", [0, 1, 2, 4])
+def test_batch_matches_alone(options):
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    defs = [(inst.sk(100, 1), 64, 30), (inst.sk(250, 2), 100, 60), (inst.gnp_maxcut(130, 0.5, 3), 33, 45),
+            (inst.moebius(400), 200, 80), (inst.gnp_maxcut(1000, 0.5, 4), 64, 25), (inst.sk(700, 5), 130, 40)]
+    problems, specs = [], []
+    for k, (J, R, tf) in enumerate(defs):
+        problems.append(nmfa.Problem(J, precision="bf16"))
+        T = torch.as_tensor(inst.schedule(tf) * (1.0 + 0.1 * k), device=dev)
+        specs.append((T, R, 100 + k, k % 3))
+    alone = [_alone(p, *sp) for p, sp in zip(problems, specs)]
+    b, outs = _batch(problems, specs, options)
+    for rep in range(2):  # a second launch (graph replay) gives the same results
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        for (s, e), (sa, ea), (J, R, tf) in zip(outs, alone, defs):
+            np.testing.assert_array_equal(s.cpu().numpy(), sa)
+            np.testing.assert_array_equal(e.cpu().numpy(), ea)
+    info = nmfa.nmfa_batch_info(b)
+    assert info["grid"] <= 152 and info["groups"] >= len(defs)
+    nmfa.nmfa_batch_destroy(b)
+    for (s, e), (J, R, tf) in zip(outs, defs):
+        sg = s.cpu().numpy()
+        for r in (0, R - 1):
+            assert e.cpu().numpy()[r] == oracle.energy_i64(J, sg[r])
+    for p in problems:
+        p.close()
+
+
+def test_tile_width_does_not_change_results():
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(300, 9)
+    p = nmfa.Problem(J, precision="bf16")
+    T = torch.as_tensor(inst.schedule(80), device=dev)
+    res = []
+    for options in (0, nmfa.NMFA_BATCH_BN64):
+        b, outs = _batch([p], [(T, 256, 3, 1)], options)
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        res.append(outs[0][0].cpu().numpy())
+        nmfa.nmfa_batch_destroy(b)
+    np.testing.assert_array_equal(res[0], res[1])
+    assert nmfa.nmfa_autotune_bn(p.handle, 256) in (64, 128)
+    p.close()
+
+
+def test_ragged_c4_like_batch():
+    # The ragged workload's shape (N ~ U[16, 1000], half SK, half G(N, 0.5)
+    # MAX-CUT, 64 replicas each) at 64 instances and t_f = 200, under a graph
+    # with autotuned tiles; sampled instances against their solo runs.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    mix = inst.ragged_batch(64, seed=7)
+    problems = [nmfa.Problem(J, precision="bf16") for _, _, J in mix]
+    T = torch.as_tensor(inst.schedule(200), device=dev)
+    specs = [(T, 64, 11, k) for k in range(len(mix))]
+    b, outs = _batch(problems, specs, nmfa.NMFA_BATCH_GRAPH | nmfa.NMFA_BATCH_AUTOTUNE)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    for k in (0, 17, 33, 63):
+        sa, ea = _alone(problems[k], *specs[k])
+        np.testing.assert_array_equal(outs[k][0].cpu().numpy(), sa)
+        np.testing.assert_array_equal(outs[k][1].cpu().numpy(), ea)
+        J = mix[k][2]
+        assert ea[5] == oracle.energy_i64(J, sa[5])
+    nmfa.nmfa_batch_destroy(b)
+    for p in problems:
+        p.close()
+
+
+# --------------------------------------------------------------------------
+# FP8-E4M3 storage of J (exact for +-1 and small integers): the run must be
+# bit-identical to the same instance stored in BF16, alone and inside a mixed
+# batch (BF16 and FP8 instances, 64- and 128-replica tiles in one batch).
+# --------------------------------------------------------------------------
+def test_fp8_storage_matches_bf16():
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(500, 21)
+    T = torch.as_tensor(inst.schedule(120), device=dev)
+    a = nmfa.Problem(J, precision="bf16")
+    f = nmfa.Problem(J, precision="bf16_fp8j")
+    assert f.info()["device_bytes"] < a.info()["device_bytes"]
+    sa, ea = _alone(a, T, 192, 4, 2)
+    sf, ef = _alone(f, T, 192, 4, 2)
+    np.testing.assert_array_equal(sa, sf)
+    np.testing.assert_array_equal(ea, ef)
+    for r in (0, 100):
+        assert ef[r] == oracle.energy_i64(J, sf[r])
+    a.close()
+    f.close()
+
+
+def test_mixed_precision_and_width_batch():
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    defs = [(inst.sk(300, 31), "bf16", 64), (inst.gnp_maxcut(450, 0.5, 32), "bf16_fp8j", 160),
+            (inst.sk(129, 33), "bf16_fp8j", 64), (inst.moebius(200), "bf16", 300)]
+    problems = [nmfa.Problem(J, precision=pr) for J, pr, _ in defs]
+    T = torch.as_tensor(inst.schedule(90), device=dev)
+    specs = [(T, R, 50 + k, k) for k, (_, _, R) in enumerate(defs)]
+    alone = [_alone(p, *sp) for p, sp in zip(problems, specs)]
+    b, outs = _batch(problems, specs, nmfa.NMFA_BATCH_GRAPH)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    for (s, e), (sa, ea) in zip(outs, alone):
+        np.testing.assert_array_equal(s.cpu().numpy(), sa)
+        np.testing.assert_array_equal(e.cpu().numpy(), ea)
+    nmfa.nmfa_batch_destroy(b)
+    for p in problems:
+        p.close()
