@@ -225,6 +225,60 @@ void nmfa_batch_destroy(nmfa_batch* b);
  * replicas) and cached for the process. */
 int nmfa_autotune_bn(nmfa_problem* p, int32_t replicas, int32_t* bn);
 
+/*
+ * Serving -- a request loop on one GPU with admission by device-memory footprint,
+ * continuous batching (every admitted request joins the next persistent launch as
+ * soon as one of `max_inflight` launch slots frees; launches overlap on the GPU)
+ * and time-to-target accounting.  A request anneals its instance with `replicas`
+ * replicas; it succeeds when some replica's energy (Eq. (1)) is <= target_energy,
+ * else it is rerun with the next noise stream id (attempt k uses stream k), at most
+ * max_attempts runs.  Each run of a request is bit-identical to running it alone.
+ * Times are seconds on the server's clock (0 = creation).
+ */
+typedef struct {
+  int64_t memory_budget_bytes;  /* device memory admitted requests may hold (<= 0: 80% of free) */
+  int32_t max_inflight;         /* concurrent launches (streams), default 2 */
+  int32_t max_attempts;         /* runs per request before giving up, default 4 */
+} nmfa_server_config;
+
+typedef struct {
+  int32_t n;
+  const double* h;              /* host, n (or NULL); copied at submit */
+  const double* J;              /* host, n*n symmetric, zero diagonal; copied at submit */
+  int32_t precision;            /* NMFA_BF16 or NMFA_BF16_FP8J */
+  const double* T;              /* host, t_f temperatures; copied */
+  int32_t t_f;
+  double sigma, alpha;
+  int32_t replicas;
+  uint64_t seed;
+  double target_energy;
+} nmfa_request;
+
+typedef struct {
+  int32_t state;        /* 0 queued, 1 admitted, 2 running, 3 done, -1 failed */
+  int32_t attempts;     /* runs started */
+  int32_t success;      /* 1 if the target was reached */
+  int32_t error;        /* NMFA_* status of a failed request */
+  double best_energy;   /* lowest energy over all runs */
+  double t_submit, t_admit, t_first_start, t_done;
+  double time_to_target;  /* t_done - t_submit when successful, else -1 */
+  int64_t spin_updates;   /* replicas * n * t_f summed over runs */
+} nmfa_result;
+
+typedef struct nmfa_server nmfa_server;
+
+int nmfa_server_create(const nmfa_server_config* cfg, nmfa_server** out);
+/* Copies the request and queues it; returns a ticket for nmfa_server_poll. */
+int nmfa_server_submit(nmfa_server* s, const nmfa_request* req, uint64_t* ticket);
+/* Current state of a request; best_signs (host n int8, or NULL) gets the best
+ * sign vector once the request is done. */
+int nmfa_server_poll(nmfa_server* s, uint64_t ticket, nmfa_result* out, int8_t* best_signs);
+/* Waits until every submitted request is done (NMFA_ETIMEOUT after timeout_s). */
+int nmfa_server_drain(nmfa_server* s, double timeout_s);
+int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding);
+/* Stops the loop (waits for launches on the GPU) and frees everything. */
+void nmfa_server_destroy(nmfa_server* s);
+
 /* Problem facts: spins, precision, 1 if h and J are integer-valued, device bytes
  * held (any pointer may be NULL). */
 int nmfa_problem_info(const nmfa_problem* p, int32_t* n, int32_t* precision,

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnmfa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["nmfa_api.cu", "k_simt.cu", "k_tc.cu"]
+SOURCES = ["nmfa_api.cu", "k_simt.cu", "k_tc.cu", "nmfa_serve.cu"]
 HEADERS = ["nmfa_internal.h", "nmfa_device.cuh", "tc_ptx.cuh"]
 
 

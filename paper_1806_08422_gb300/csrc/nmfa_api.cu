@@ -130,22 +130,21 @@ bool bf16_exact(double v) {
   return (bits & 0xFFFFu) == 0u;
 }
 
-// All finite E4M3 values (bias 7, 3 mantissa bits, no infinities; S.1111.111 is NaN).
+// Exactly representable in FP8 E4M3 (bias 7, 3 mantissa bits, largest finite
+// 448, subnormals k * 2^-9 for k = 1..7): |v| = m * 2^e with a 3-bit fraction.
 bool e4m3_exact(double v) {
-  static std::vector<double> table = [] {
-    std::vector<double> t;
-    for (int b = 0; b < 256; ++b) {
-      const int sgn = (b >> 7) & 1, ex = (b >> 3) & 15, man = b & 7;
-      if (ex == 15 && man == 7) continue;
-      double mag = (ex == 0) ? std::ldexp(static_cast<double>(man), -9)
-                             : std::ldexp(1.0 + man / 8.0, ex - 7);
-      t.push_back(sgn ? -mag : mag);
-    }
-    return t;
-  }();
-  for (double x : table)
-    if (x == v) return true;
-  return false;
+  if (v == 0.0) return true;
+  const double a = std::fabs(v);
+  if (!(a <= 448.0)) return false;
+  int e = 0;
+  const double fr = std::frexp(a, &e);  // a = fr * 2^e, fr in [0.5, 1)
+  const int exp_unbiased = e - 1;       // a = (2 fr) * 2^(e-1), 2 fr in [1, 2)
+  if (exp_unbiased < -6) {              // subnormal range: multiples of 2^-9
+    const double k = std::ldexp(a, 9);
+    return k == std::floor(k) && k >= 1.0 && k <= 7.0;
+  }
+  const double mant8 = (2.0 * fr - 1.0) * 8.0;  // exact in binary64
+  return mant8 == std::floor(mant8);
 }
 
 int validate_common(int32_t n, int32_t precision) {
@@ -295,6 +294,17 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
     if ((rc = launch_convert_dense(n, p->J64, p->J8, 3, n, ld8, st))) return fail(rc);
   }
   if ((rc = cuda_error(cudaStreamSynchronize(st), "create conversions"))) return fail(rc);
+  // Tensor-path problems with integer couplings keep only the compact copies: the
+  // FP64 matrix served the row norms and is not read again (energies use int8).
+  if ((precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) && int8_ok) {
+    auto it = std::find(p->allocations.begin(), p->allocations.end(), static_cast<void*>(p->J64));
+    if (it != p->allocations.end()) {
+      cudaFree(p->J64);
+      p->allocations.erase(it);
+      p->device_bytes -= static_cast<int64_t>(sizeof(double)) * n * n;
+      p->J64 = nullptr;
+    }
+  }
   *out = p;
   return NMFA_OK;
 }

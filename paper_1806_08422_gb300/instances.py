@@ -194,3 +194,41 @@ def make_instance(kind: str, n: int, seed: int) -> np.ndarray:
     if kind == "regular3":
         return regular3(n, seed)
     raise ValueError(kind)
+
+
+# ----------------------------------------------------------------------------
+# Gset files (the format of the G22/G39 instances of Table I): a header line
+# "n m" followed by m lines "i j w" with 1-based vertices; J_ij = w per edge, so the
+# Ising energy H of Eq. (1) and the cut value relate by cut = (W - H) / 2 with
+# W = sum_{i<j} J_ij (Table I reports cut values).  The files themselves are not
+# shipped; a user who has them can reproduce Table I's setting.
+# ----------------------------------------------------------------------------
+def read_gset(path: str):
+    """Returns (n, J) with J dense float64 symmetric, zero diagonal."""
+    with open(path) as f:
+        head = f.readline().split()
+        n, m = int(head[0]), int(head[1])
+        J = np.zeros((n, n))
+        for _ in range(m):
+            parts = f.readline().split()
+            i, j, w = int(parts[0]) - 1, int(parts[1]) - 1, float(parts[2]) if len(parts) > 2 else 1.0
+            if i == j:
+                raise ValueError("self-loop in Gset file")
+            J[i, j] += w
+            J[j, i] += w
+    return n, J
+
+
+def write_gset(path: str, J: np.ndarray):
+    n = J.shape[0]
+    iu = np.argwhere(np.triu(J, 1) != 0)
+    with open(path, "w") as f:
+        f.write("%d %d\n" % (n, len(iu)))
+        for i, j in iu:
+            w = J[i, j]
+            f.write("%d %d %s\n" % (i + 1, j + 1, repr(int(w)) if float(w).is_integer() else repr(float(w))))
+
+
+def cut_value(J: np.ndarray, energy: float) -> float:
+    """MAX-CUT value of a sign vector with Ising energy `energy` (h = 0)."""
+    return 0.5 * (float(np.triu(J, 1).sum()) - energy)

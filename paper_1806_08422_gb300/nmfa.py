@@ -47,6 +47,12 @@ SIGNATURES = {
     "nmfa_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "nmfa_batch_destroy": (None, [_P]),
     "nmfa_autotune_bn": (ctypes.c_int, [_P, _i32, _P]),
+    "nmfa_server_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "nmfa_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(_u64)]),
+    "nmfa_server_poll": (ctypes.c_int, [_P, _u64, _P, _P]),
+    "nmfa_server_drain": (ctypes.c_int, [_P, _f64]),
+    "nmfa_server_stats": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nmfa_server_destroy": (None, [_P]),
     "nmfa_debug_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _i32, _P, _P, _P, _P, _P,
                                       _P, _P]),
     "nmfa_problem_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -249,6 +255,69 @@ def nmfa_autotune_bn(handle, replicas):
     bn = ctypes.c_int32()
     _check(load().nmfa_autotune_bn(handle, int(replicas), ctypes.byref(bn)))
     return bn.value
+
+
+class nmfa_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_attempts", ctypes.c_int32)]
+
+
+class nmfa_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("h", ctypes.c_void_p), ("J", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("T", ctypes.c_void_p), ("t_f", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("replicas", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("target_energy", ctypes.c_double)]
+
+
+class nmfa_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("attempts", ctypes.c_int32), ("success", ctypes.c_int32),
+                ("error", ctypes.c_int32), ("best_energy", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_first_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("time_to_target", ctypes.c_double), ("spin_updates", ctypes.c_int64)]
+
+
+def nmfa_server_create(memory_budget_bytes=0, max_inflight=2, max_attempts=4):
+    cfg = nmfa_server_config(int(memory_budget_bytes), int(max_inflight), int(max_attempts))
+    out = ctypes.c_void_p()
+    _check(load().nmfa_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def nmfa_server_submit(server, J, T, replicas, target_energy, h=None, precision="bf16_fp8j", sigma=0.15,
+                       alpha=0.15, seed=0):
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    h = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    q = nmfa_request(J.shape[0], None if h is None else h.ctypes.data, J.ctypes.data,
+                     PRECISIONS.get(precision, precision), T.ctypes.data, T.shape[0], float(sigma), float(alpha),
+                     int(replicas), int(seed), float(target_energy))
+    ticket = ctypes.c_uint64()
+    _check(load().nmfa_server_submit(server, ctypes.byref(q), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def nmfa_server_poll(server, ticket, n=None):
+    res = nmfa_result()
+    signs = np.zeros(n, dtype=np.int8) if n else None
+    _check(load().nmfa_server_poll(server, int(ticket), ctypes.byref(res), _np_ptr(signs)))
+    d = {k: getattr(res, k) for k, _ in nmfa_result._fields_}
+    if signs is not None:
+        d["best_signs"] = signs
+    return d
+
+
+def nmfa_server_drain(server, timeout_s=600.0):
+    _check(load().nmfa_server_drain(server, float(timeout_s)))
+
+
+def nmfa_server_stats(server):
+    la, mu, out = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(load().nmfa_server_stats(server, ctypes.byref(la), ctypes.byref(mu), ctypes.byref(out)))
+    return {"launches": la.value, "mem_used": mu.value, "outstanding": out.value}
+
+
+def nmfa_server_destroy(server):
+    load().nmfa_server_destroy(server)
 
 
 # ---------------------------------------------------------------- convenience

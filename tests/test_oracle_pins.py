@@ -325,3 +325,18 @@ def test_fig3_moebius16_qualitative():
     e = out["energy_i64"]
     assert e.min() == -20
     assert np.mean(e <= -16) > 0.5
+
+
+def test_gset_roundtrip_and_cut_value(tmp_path):
+    # Table I reports MAX-CUT values: cut = (W - H)/2; a ring of 10 has a perfect
+    # cut of 10 edges at the ground energy -10.
+    J = inst.ring(10)
+    path = str(tmp_path / "ring.gset")
+    inst.write_gset(path, J)
+    n, J2 = inst.read_gset(path)
+    assert n == 10 and np.array_equal(J, J2)
+    e, best, _ = oracle.brute_force(J2)
+    assert inst.cut_value(J2, e) == 10.0
+    Jm = inst.moebius(16)
+    e, _, _ = oracle.brute_force(Jm)
+    assert inst.cut_value(Jm, e) == 22.0
