@@ -59,10 +59,11 @@ constexpr int kColsPerWarp = 32;
 constexpr int kStages = 6;
 constexpr uint32_t kABytes = kBM * 128;
 constexpr uint32_t kStageBytes = kABytes + kBNMax * 128;
-// TMEM columns: accumulator [0, 128), FP32 master state [128, 256), noise [256, 384)
+// TMEM columns: two accumulators [0, 128) and [128, 256) (step g uses g % 2),
+// FP32 master state [256, 384).
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColMaster = kBNMax;
-constexpr uint32_t kColNoise = 2 * kBNMax;
+constexpr uint32_t kColAcc1 = kBNMax;
+constexpr uint32_t kColMaster = 2 * kBNMax;
 constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A CTA that reaches a new group early waits for the group's other CTAs to finish
@@ -95,7 +96,7 @@ struct SharedCtl {
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t acc_full;
-  uint64_t acc_empty;
+  uint64_t bias_ready;   // the step's accumulator holds its bias (epilogue -> MMA)
   uint64_t drain;
   uint32_t tmem_slot;
   int32_t abort_flag;
@@ -155,6 +156,34 @@ __device__ __forceinline__ void acquire_tensormap(const void* m) {
                : "memory");
 }
 
+// (A) the bias of one step, h_i + sigma z d_i, written into the accumulator the step
+// will use (the Gaussian draws do not depend on the state, so this runs while the
+// tensor core still computes the previous step), then signalled to the MMA issuer.
+__device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base, int col0, int rbase, int i,
+                                           uint32_t stream, const RoundKeys& rk, float sigma_ns, float dd, float hi,
+                                           int lane, SharedCtl* ctl) {
+  const uint32_t acc = lane_base + ((g & 1u) ? kColAcc1 : 0u);
+  uint32_t v[16];
+#pragma unroll 1
+  for (int cc = 0; cc < kColsPerWarp; cc += 16) {
+#pragma unroll
+    for (int gq = 0; gq < 4; ++gq) {
+      const int r4 = rbase + cc + 4 * gq;
+      const float4 z = gauss4_f32_fast(philox4x32_10_rk(
+          make_uint4(static_cast<uint32_t>(r4 >> 2), static_cast<uint32_t>(t), static_cast<uint32_t>(i), stream), rk));
+      v[4 * gq + 0] = __float_as_uint(fmaf(sigma_ns * z.x, dd, hi));
+      v[4 * gq + 1] = __float_as_uint(fmaf(sigma_ns * z.y, dd, hi));
+      v[4 * gq + 2] = __float_as_uint(fmaf(sigma_ns * z.z, dd, hi));
+      v[4 * gq + 3] = __float_as_uint(fmaf(sigma_ns * z.w, dd, hi));
+    }
+    ptx::tmem_st16(acc + col0 + cc, v);
+  }
+  ptx::tmem_wait_st();
+  ptx::tc_fence_before();
+  __syncwarp();
+  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready));
+}
+
 // Epilogue warps' work for one item (one 128-spin tile of one group), from the
 // initial state through t_f steps to the readout.  Warp e serves TMEM lane quarter
 // q = (e + 2) % 4 (spins 32q..32q+31 of the tile) and column group e / 4 (32
@@ -206,66 +235,56 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   __syncwarp();
   if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
 
+  // Row constants: with d_i > 0 the accumulator starts at h_i + sigma z d_i so that
+  // acc / d_i = (h_i + sum_j J_ij s_j) / d_i + sigma z; a spin with d_i = 0 (no
+  // couplings, no field) starts at sigma z and is scaled by 1.
+  const float dd = inv_d > 0.0f ? 1.0f / inv_d : 1.0f;
+  const float sc = inv_d > 0.0f ? inv_d : 1.0f;
+  // (A) the bias of step t: the Gaussian draws do not depend on the state, so they
+  // are generated while the tensor core still computes the previous step
+  if (t_f > 0) write_bias(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+
   for (int t = 0; t < t_f; ++t, ++gstep) {
     float inv_T = 0.0f;
     if (lane == 0) inv_T = 1.0f / static_cast<float>(T[t]);  // one FP64 load+convert per warp
     inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
     __nv_bfloat16* Snext = S16 + static_cast<size_t>((t + 1) & 1) * plane;
-    // (A) the step's Gaussian draws do not depend on the state: generate them while
-    // the tensor core computes this step's product, and park them in TMEM
-#pragma unroll 1
-    for (int cc = 0; cc < kCW; cc += 16) {
-#pragma unroll
-      for (int gq = 0; gq < 4; ++gq) {
-        const int r4 = rbase + cc + 4 * gq;
-        const float4 z = gauss4_f32_fast(philox4x32_10_rk(
-            make_uint4(static_cast<uint32_t>(r4 >> 2), static_cast<uint32_t>(t), static_cast<uint32_t>(i), stream), rk));
-        v[4 * gq + 0] = __float_as_uint(sigma_ns * z.x);
-        v[4 * gq + 1] = __float_as_uint(sigma_ns * z.y);
-        v[4 * gq + 2] = __float_as_uint(sigma_ns * z.z);
-        v[4 * gq + 3] = __float_as_uint(sigma_ns * z.w);
-      }
-      ptx::tmem_st16(lane_base + kColNoise + col0 + cc, v);
-    }
-    ptx::tmem_wait_st();
+    // the next step's bias goes into the other accumulator (read last two steps ago)
+    if (t + 1 < t_f) write_bias(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
     ptx::tc_fence_after();
+    const uint32_t acc = lane_base + ((gstep & 1u) ? kColAcc1 : 0u);
     const bool write_phi = (t == t_f - 1) && phi_out != nullptr;
-#pragma unroll 1
+#pragma unroll
     for (int cc = 0; cc < kCW; cc += 16) {
-      uint32_t zn[16];
-      ptx::tmem_ld16(lane_base + col0 + cc, v);
-      ptx::tmem_ld16(lane_base + kColMaster + col0 + cc, m);
-      ptx::tmem_ld16(lane_base + kColNoise + col0 + cc, zn);
+      uint32_t pa[16], ms[16];
+      ptx::tmem_ld16(acc + col0 + cc, pa);
+      ptx::tmem_ld16(lane_base + kColMaster + col0 + cc, ms);
       ptx::tmem_wait_ld();
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const float P = __uint_as_float(v[k]) + hi;
-        const float phi = fmaf(P, inv_d, __uint_as_float(zn[k]));
+        const float phi = __uint_as_float(pa[k]) * sc;
         const float sh = -ptx::tanh_approx(phi * inv_T);
-        const float s_new = fmaf(alpha, sh, oma * __uint_as_float(m[k]));
-        m[k] = __float_as_uint(s_new);
-        v[k] = __float_as_uint(phi);
+        const float s_new = fmaf(alpha, sh, oma * __uint_as_float(ms[k]));
+        ms[k] = __float_as_uint(s_new);
+        pa[k] = __float_as_uint(phi);
       }
       if (write_phi) {  // last step of a debug run only (warp-uniform branch)
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int r = rbase + cc + k;
-          if (valid && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(__uint_as_float(v[k]));
+          if (valid && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(__uint_as_float(pa[k]));
         }
       }
-      ptx::tmem_st16(lane_base + kColMaster + col0 + cc, m);
+      ptx::tmem_st16(lane_base + kColMaster + col0 + cc, ms);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         Snext[static_cast<size_t>(col0 + cc + k) * n_pad + i] =
-            valid ? __float2bfloat16_rn(__uint_as_float(m[k])) : __float2bfloat16_rn(0.0f);
+            valid ? __float2bfloat16_rn(__uint_as_float(ms[k])) : __float2bfloat16_rn(0.0f);
       }
     }
     ptx::tmem_wait_st();
-    ptx::tc_fence_before();
-    __syncwarp();
-    if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->acc_empty));
     ptx::fence_proxy_async_global();
     __syncwarp();
     if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
@@ -309,7 +328,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       ptx::mbar_init(ptx::smem_u32(&ctl.empty[s]), 1);
     }
     ptx::mbar_init(ptx::smem_u32(&ctl.acc_full), 1);
-    ptx::mbar_init(ptx::smem_u32(&ctl.acc_empty), kEpiWarps);
+    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready), kEpiWarps);
     ptx::mbar_init(ptx::smem_u32(&ctl.drain), 1);
     ctl.abort_flag = 0;
     ptx::fence_mbar_init();
@@ -428,11 +447,12 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
         const int KB = g->n_pad / kBK, t_f = g->t_f;
         const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
         for (int t = 0; t < t_f && ok; ++t, ++gstep) {
-          if (gstep > 0) {
-            ok = wait_bar(ptx::smem_u32(&ctl.acc_empty), (gstep - 1) & 1u, &ctl, status);
-            if (!ok) break;
-          }
+          // the epilogue has written this step's bias (h + sigma z d) into the
+          // accumulator the step uses; the product accumulates onto it
+          ok = wait_bar(ptx::smem_u32(&ctl.bias_ready), gstep & 1u, &ctl, status);
+          if (!ok) break;
           ptx::tc_fence_after();
+          const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
           for (int kb = 0; kb < KB; ++kb) {
             const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
             ok = wait_bar(ptx::smem_u32(&ctl.full[stage]), phase, &ctl, status);
@@ -442,8 +462,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
             const uint32_t sB = sA + kABytes;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
-              ptx::mma_bf16(tmem, ptx::sw128_desc(sA + kk * 32), ptx::sw128_desc(sB + kk * 32), idesc,
-                            (kb | kk) != 0 ? 1u : 0u);
+              ptx::mma_bf16(acc, ptx::sw128_desc(sA + kk * 32), ptx::sw128_desc(sB + kk * 32), idesc, 1u);
             }
             issued = true;
             ptx::mma_commit(ptx::smem_u32(&ctl.empty[stage]));
