@@ -9,8 +9,9 @@
 //     slices of a step start before the step's state is published, the S slices
 //     after the whole warp has seen every row block's epoch flag of the replica
 //     block reach the step;
-//   - warp 1 (one lane) issues tcgen05.mma (M = 128, N = BN, K = 16) into a TMEM
-//     accumulator, releasing ring slots and the accumulator with tcgen05.commit;
+//   - warp 1 issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of the
+//     converged warp) into a TMEM accumulator, releasing ring slots and the
+//     accumulator with tcgen05.commit;
 //   - warps 2..17 first draw the step's noise (Philox/Box-Muller, independent of
 //     the state) while the tensor core works and park sigma*z in TMEM; once the
 //     accumulator is complete they read it with tcgen05.ld and finish the step:
@@ -347,13 +348,12 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     // Per step: claim the first ring slots and start their J slices at once (J
     // does not depend on the previous step), wait with the whole warp until every
     // row block of the group has published the step's state, then issue the S
-    // slices of the claimed slots and stream the rest of the step.
-    uint32_t it = 0;        // ring iterations whose J and S copies are both issued
-    int pending = 0;        // claimed slots with only the J copy issued
+    // slices of the claimed slots and stream the rest of the step.  The whole warp
+    // runs the loop; one elected lane issues each copy.
+    const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
+    uint32_t stage = 0, phase = 0;  // next ring slot to fill
+    uint32_t filled = 0;            // ring slots whose copies were issued (for the drain)
     bool ok = true;
-    const void* tmS_cur = nullptr;
-    int kslice_base = 0, KB_cur = 1;
-#define NMFA_KSLICE(kb) ((kb) + kslice_base >= KB_cur ? (kb) + kslice_base - KB_cur : (kb) + kslice_base)
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
@@ -362,9 +362,10 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       const void* tmS = &g->tmS;
       const uint32_t* gflags = g->flags;
       const uint32_t stage_tx = kABytes + static_cast<uint32_t>(bn) * 128u;
-      KB_cur = n_pad / kBK;
-      kslice_base = 2 * b;
-      tmS_cur = tmS;
+      const int KB = n_pad / kBK;
+      // every row block starts its K sweep at a different slice (2 b) to spread the
+      // CTAs' reads of J and S over L2
+      const int kslice_base = (2 * b) % KB;
       if (lane == 0) {
         acquire_tensormap(tmJ);
         acquire_tensormap(tmS);
@@ -372,112 +373,118 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
         ptx::tma_prefetch_desc(tmS);
       }
       __syncwarp();
-      const int pre = KB_cur < kStages ? KB_cur : kStages;
+      const int pre = KB < kStages ? KB : kStages;
       for (int t = 0; t < t_f && ok; ++t) {
         const int sy = (t & 1) * bn;
-        if (lane == 0) {
-          for (int kb = 0; kb < pre; ++kb) {
-            const uint32_t k = it + kb, stage = k % kStages, phase = (k / kStages) & 1u;
-            ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, status);
-            if (!ok) break;
-            const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
-            ptx::mbar_arrive_expect_tx(full, stage_tx);
-            ptx::tma_load_2d(ring + stage * kStageBytes, tmJ, NMFA_KSLICE(kb) * kBK, b * kBM, full);
-            pending = kb + 1;
+        const uint32_t claim_stage = stage;
+        int claimed = 0;
+        int ks = kslice_base;  // K slice of loop index kb
+        for (int kb = 0; kb < pre; ++kb) {
+          ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
+          if (!ok) break;
+          ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
+          ptx::tma_load_2d_warp(ring + stage * kStageBytes, tmJ, ks * kBK, b * kBM, full0 + 8u * stage);
+          ++claimed;
+          ++filled;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
           }
+          if (++ks == KB) ks = 0;
         }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        if (!ok) break;
-        ok = wait_group_flags(gflags, nb, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
-                              t == 0 ? kStartTimeoutNs : kTimeoutNs);
+        if (ok)
+          ok = wait_group_flags(gflags, nb, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
+                                t == 0 ? kStartTimeoutNs : kTimeoutNs);
         // each lane acquired its own row blocks' counters; the warp barrier orders
-        // those acquires before lane 0's copies (memory ordering within the warp)
+        // those acquires before the elected lane's copies (memory ordering within the warp)
         __syncwarp();
-        if (lane == 0) {
-          if (ok) ptx::fence_proxy_async_global();
-          // the S halves of the claimed slots (also on abort, so that their barriers complete)
-          for (int kb = 0; kb < pending; ++kb) {
-            const uint32_t k = it + kb, stage = k % kStages;
-            ptx::tma_load_2d(ring + stage * kStageBytes + kABytes, tmS, NMFA_KSLICE(kb) * kBK, sy,
-                             ptx::smem_u32(&ctl.full[stage]));
-          }
-          it += pending;
-          pending = 0;
-          for (int kb = pre; kb < KB_cur && ok; ++kb) {
-            const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
-            ok = wait_bar(ptx::smem_u32(&ctl.empty[stage]), phase ^ 1u, &ctl, status);
-            if (!ok) break;
-            const uint32_t full = ptx::smem_u32(&ctl.full[stage]);
-            const uint32_t sA = ring + stage * kStageBytes;
-            ptx::mbar_arrive_expect_tx(full, stage_tx);
-            ptx::tma_load_2d(sA, tmJ, NMFA_KSLICE(kb) * kBK, b * kBM, full);
-            ptx::tma_load_2d(sA + kABytes, tmS, NMFA_KSLICE(kb) * kBK, sy, full);
-            ++it;
+        if (ok) ptx::fence_proxy_async_global();
+        // the S halves of the claimed slots (also on abort, so that their barriers complete)
+        {
+          uint32_t st = claim_stage;
+          int ks2 = kslice_base;
+          for (int kb = 0; kb < claimed; ++kb) {
+            ptx::tma_load_2d_warp(ring + st * kStageBytes + kABytes, tmS, ks2 * kBK, sy, full0 + 8u * st);
+            if (++st == kStages) st = 0;
+            if (++ks2 == KB) ks2 = 0;
           }
         }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        for (int kb = pre; kb < KB; ++kb) {
+          ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
+          if (!ok) break;
+          const uint32_t sA = ring + stage * kStageBytes;
+          ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
+          ptx::tma_load_2d_warp(sA, tmJ, ks * kBK, b * kBM, full0 + 8u * stage);
+          ptx::tma_load_2d_warp(sA + kABytes, tmS, ks * kBK, sy, full0 + 8u * stage);
+          ++filled;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+          if (++ks == KB) ks = 0;
+        }
       }
     }
-    if (!ok && lane == 0) {
-      // J-only slots claimed before a failed wait get their S copy so their barriers complete
-      for (int kb = 0; kb < pending; ++kb) {
-        const uint32_t k = it + kb, stage = k % kStages;
-        ptx::tma_load_2d(ring + stage * kStageBytes + kABytes, tmS_cur, NMFA_KSLICE(kb) * kBK, 0,
-                         ptx::smem_u32(&ctl.full[stage]));
-      }
-      it += pending;
-      // drain: wait (bounded) until every copy this thread issued has landed
-      const uint32_t last = it;
+    if (!ok) {
+      // drain: wait (bounded) until every copy issued into the last ring slots has landed
+      const uint32_t last = filled;
       for (uint32_t k = (last > static_cast<uint32_t>(kStages) ? last - kStages : 0u); k < last; ++k) {
-        const uint32_t stage = k % kStages, phase = (k / kStages) & 1u;
+        const uint32_t st = k % kStages, ph = (k / kStages) & 1u;
         const uint64_t t0 = ptx::globaltimer_ns();
-        while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.full[stage]), phase) && ptx::globaltimer_ns() - t0 < kDrainNs) {
+        while (!ptx::mbar_try_wait(full0 + 8u * st, ph) && ptx::globaltimer_ns() - t0 < kDrainNs) {
         }
       }
     }
-#undef NMFA_KSLICE
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      uint32_t it = 0, gstep = 0;
-      bool ok = true;
-      bool issued = false;
-      for (int w = w_begin; w < w_end && ok; ++w) {
-        const TcGroup* g = groups + items[w].group;
-        const int KB = g->n_pad / kBK, t_f = g->t_f;
-        const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
-        for (int t = 0; t < t_f && ok; ++t, ++gstep) {
-          // the epilogue has written this step's bias (h + sigma z d) into the
-          // accumulator the step uses; the product accumulates onto it
-          ok = wait_bar(ptx::smem_u32(&ctl.bias_ready), gstep & 1u, &ctl, status);
+    // The whole warp runs the loop and one elected lane issues each tcgen05.mma and
+    // commit.  The ring position is carried as (stage, phase) counters and the
+    // shared-memory descriptors are formed once and advanced by adding to their
+    // start-address field (32 bytes per K = 16 step, one stage per ring slot; the
+    // field cannot carry out of its 14 bits because shared addresses stay below 256 KB).
+    uint32_t stage = 0, phase = 0, gstep = 0;
+    bool ok = true;
+    bool issued = false;
+    const uint64_t desc0 = ptx::sw128_desc(ring);
+    constexpr uint64_t kDescStage = kStageBytes >> 4, kDescB = kABytes >> 4, kDescK = 32 >> 4;
+    const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
+    for (int w = w_begin; w < w_end && ok; ++w) {
+      const TcGroup* g = groups + items[w].group;
+      const int KB = g->n_pad / kBK, t_f = g->t_f;
+      const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
+      for (int t = 0; t < t_f && ok; ++t, ++gstep) {
+        // the epilogue has written this step's bias (h + sigma z d) into the
+        // accumulator the step uses; the product accumulates onto it
+        ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.bias_ready), gstep & 1u, &ctl, status));
+        if (!ok) break;
+        ptx::tc_fence_after();
+        const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
+        for (int kb = 0; kb < KB; ++kb) {
+          // the stage's TMA copies completed on its full barrier (async proxy to async proxy)
+          ok = __all_sync(0xffffffffu, wait_bar(full0 + 8u * stage, phase, &ctl, status));
           if (!ok) break;
-          ptx::tc_fence_after();
-          const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
-          for (int kb = 0; kb < KB; ++kb) {
-            const uint32_t stage = it % kStages, phase = (it / kStages) & 1u;
-            ok = wait_bar(ptx::smem_u32(&ctl.full[stage]), phase, &ctl, status);
-            if (!ok) break;
-            ptx::tc_fence_after();
-            const uint32_t sA = ring + stage * kStageBytes;
-            const uint32_t sB = sA + kABytes;
+          const uint64_t da = desc0 + kDescStage * stage;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-              ptx::mma_bf16(acc, ptx::sw128_desc(sA + kk * 32), ptx::sw128_desc(sB + kk * 32), idesc, 1u);
-            }
-            issued = true;
-            ptx::mma_commit(ptx::smem_u32(&ctl.empty[stage]));
-            ++it;
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            ptx::mma_bf16_warp(acc, da + kDescK * kk, da + kDescB + kDescK * kk, idesc);
           }
-          if (!ok) break;
-          ptx::mma_commit(ptx::smem_u32(&ctl.acc_full));
+          issued = true;
+          ptx::mma_commit_warp(empty0 + 8u * stage);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
+        if (!ok) break;
+        ptx::mma_commit_warp(ptx::smem_u32(&ctl.acc_full));
       }
-      if (!ok && issued) {
-        // drain: wait (bounded) for every MMA issued so far
-        ptx::mma_commit(ptx::smem_u32(&ctl.drain));
-        const uint64_t t0 = ptx::globaltimer_ns();
-        while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.drain), 0u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
-        }
+    }
+    if (!ok && issued) {
+      // drain: wait (bounded) for every MMA issued so far
+      ptx::mma_commit_warp(ptx::smem_u32(&ctl.drain));
+      const uint64_t t0 = ptx::globaltimer_ns();
+      while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.drain), 0u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
       }
     }
   } else {
