@@ -248,7 +248,9 @@ def main():
 
     peaks, peak_kind = _peaks()
     kern_ms = statistics.mean(kernel_ms)
-    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * args.tf
+    # t_f products J S (2 N^2 R each) plus, on the tensor path, the energy product J s~
+    # the kernel forms after the last step
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * (args.tf + (1 if args.precision == "bf16" else 0))
     if args.precision == "bf16":
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         achieved = flops / (kern_ms / 1e3) / 1e12

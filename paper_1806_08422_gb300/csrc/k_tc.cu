@@ -85,6 +85,11 @@ struct __align__(64) TcGroup {
   int8_t* signs;
   __nv_bfloat16* S16;     // [2][bn][n_pad]
   uint32_t* flags;        // [nb] epoch counters
+  int64_t* e2h;           // [bn] 2H of the group's replicas, accumulated (zeroed every launch)
+  uint32_t* e_done;       // epilogue warps that have added their part of 2H (zeroed every launch)
+  double* energy;         // instance-level [replicas] or null
+  int64_t* energy_i64;    // instance-level [replicas] or null
+  int32_t energy_pass;    // 1: the run ends with the energy product J s~ (see epilogue_item)
   int32_t n, n_pad, bn, replicas, r0, t_f;
   float sigma_ns, alpha, one_m_alpha;
   uint32_t seed_lo, seed_hi, stream;
@@ -97,7 +102,13 @@ struct SharedCtl {
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t acc_full;
-  uint64_t bias_ready;   // the step's accumulator holds its bias (epilogue -> MMA)
+  // The step's accumulator holds its bias (epilogue -> MMA).  Step g uses
+  // bias_ready[g % 2]: every epilogue warp arrives for step g + 1 before it waits for
+  // step g's product, so with one barrier a fast warp's arrival for g + 1 could
+  // complete step g's phase before a slow warp has written step g's bias.  Between two
+  // uses of the same barrier each warp waits for acc_full of the step in between,
+  // which implies the earlier phase completed.
+  uint64_t bias_ready[2];
   uint64_t drain;
   uint32_t tmem_slot;
   int32_t abort_flag;
@@ -182,7 +193,75 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
-  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready));
+  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready[g & 1u]));
+}
+
+// (A') the accumulator start of the energy product: 2 h_i, no noise.
+__device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base, int col0, float hi, int lane,
+                                                  SharedCtl* ctl) {
+  const uint32_t acc = lane_base + ((g & 1u) ? kColAcc1 : 0u);
+  uint32_t v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __float_as_uint(2.0f * hi);
+#pragma unroll 1
+  for (int cc = 0; cc < kColsPerWarp; cc += 16) ptx::tmem_st16(acc + col0 + cc, v);
+  ptx::tmem_wait_st();
+  ptx::tc_fence_before();
+  __syncwarp();
+  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready[g & 1u]));
+}
+
+// (C) Energy readout (Eq. 1) of one warp's 32 spins x 32 replicas.  The accumulator
+// of the energy product started at 2 h_i, so it holds P_i = 2 h_i + sum_j J_ij s~_j,
+// and sum_i s~_i P_i = 2 H(s~) because J is symmetric with zero diagonal.  Every
+// partial sum is an integer below 2^24, so the FP32 accumulator holds P_i exactly and
+// the sums over spins are taken in integers.  Each warp adds its part to the group's
+// 2H sums; the warp that adds the group's last part (`parts` in all) writes the
+// energies.  Kept out of line: it runs once per item and its registers would
+// otherwise weigh on the step loop.
+__device__ __noinline__ void energy_readout(const TcGroup* __restrict__ g, uint32_t acc, uint32_t master, int col0,
+                                            int rbase, bool valid, int lane, uint32_t parts) {
+  const int R = g->replicas;
+  int mine = 0;  // lane c: this warp's part of 2H for column col0 + c
+#pragma unroll 1
+  for (int cc = 0; cc < kColsPerWarp; cc += 16) {
+    uint32_t pa[16], ms[16];
+    ptx::tmem_ld16(acc + col0 + cc, pa);
+    ptx::tmem_ld16(master + col0 + cc, ms);
+    ptx::tmem_wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = rbase + cc + k;
+      int v = 0;
+      if (valid && r < R) {
+        const int pi = __float2int_rn(__uint_as_float(pa[k]));
+        v = __uint_as_float(ms[k]) >= 0.0f ? pi : -pi;
+      }
+      const int sum = __reduce_add_sync(0xffffffffu, v);  // 32 spins, |sum| < 2^29
+      if (lane == cc + k) mine = sum;
+    }
+  }
+  if (rbase + lane < R)
+    atomicAdd(reinterpret_cast<unsigned long long*>(g->e2h + col0 + lane),
+              static_cast<unsigned long long>(static_cast<long long>(mine)));
+  // each warp fences its additions before counting itself done
+  __threadfence();
+  __syncwarp();
+  uint32_t prev = 0;
+  if (lane == 0) prev = atomicAdd(g->e_done, 1u);
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev + 1 == parts) {
+    __threadfence();
+    for (int c = lane; c < g->bn; c += 32) {
+      const int r = g->r0 + c;
+      if (r < R) {
+        const long long e2 = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(g->e2h + c), 0ull));
+        const long long H = e2 / 2;  // 2H is even: sum_i s~_i (J s~)_i counts every pair twice
+        if (g->energy_i64 != nullptr) g->energy_i64[r] = H;
+        if (g->energy != nullptr) g->energy[r] = static_cast<double>(H);
+      }
+    }
+  }
 }
 
 // Epilogue warps' work for one item (one 128-spin tile of one group), from the
@@ -206,6 +285,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   const size_t plane = static_cast<size_t>(BN) * n_pad;
   const RoundKeys rk = make_round_keys(NoiseKey{g->seed_lo, g->seed_hi});
   const float sigma_ns = g->sigma_ns, alpha = g->alpha, oma = g->one_m_alpha;
+  const int energy_pass = g->energy_pass;
   const uint32_t stream = g->stream;
   const double* T = g->T;
   double* phi_out = g->phi_out;
@@ -251,12 +331,17 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
     __nv_bfloat16* Snext = S16 + static_cast<size_t>((t + 1) & 1) * plane;
     // the next step's bias goes into the other accumulator (read last two steps ago)
-    if (t + 1 < t_f) write_bias(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+    if (t + 1 < t_f)
+      write_bias(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+    else if (energy_pass)
+      write_energy_bias(gstep + 1, lane_base, col0, hi, lane, ctl);
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
     ptx::tc_fence_after();
     const uint32_t acc = lane_base + ((gstep & 1u) ? kColAcc1 : 0u);
     const bool write_phi = (t == t_f - 1) && phi_out != nullptr;
+    // the last step hands the energy product the sign vector s~ instead of s
+    const bool write_sign = energy_pass && t == t_f - 1;
 #pragma unroll
     for (int cc = 0; cc < kCW; cc += 16) {
       uint32_t pa[16], ms[16];
@@ -281,8 +366,9 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
       ptx::tmem_st16(lane_base + kColMaster + col0 + cc, ms);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        Snext[static_cast<size_t>(col0 + cc + k) * n_pad + i] =
-            valid ? __float2bfloat16_rn(__uint_as_float(ms[k])) : __float2bfloat16_rn(0.0f);
+        float sv = __uint_as_float(ms[k]);
+        if (write_sign) sv = sv >= 0.0f ? 1.0f : -1.0f;
+        Snext[static_cast<size_t>(col0 + cc + k) * n_pad + i] = valid ? __float2bfloat16_rn(sv) : __float2bfloat16_rn(0.0f);
       }
     }
     ptx::tmem_wait_st();
@@ -308,6 +394,14 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
       }
     }
   }
+  // (C) energy readout (Eq. 1), after the energy product of the last step's signs
+  if (energy_pass) {
+    if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
+    ptx::tc_fence_after();
+    energy_readout(g, lane_base + ((gstep & 1u) ? kColAcc1 : 0u), lane_base + kColMaster, col0, rbase, valid, lane,
+                   static_cast<uint32_t>(n_pad / kBM) * static_cast<uint32_t>(BN / 8));
+    ++gstep;
+  }
   return true;
 }
 
@@ -329,7 +423,8 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       ptx::mbar_init(ptx::smem_u32(&ctl.empty[s]), 1);
     }
     ptx::mbar_init(ptx::smem_u32(&ctl.acc_full), 1);
-    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready), kEpiWarps);
+    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready[0]), kEpiWarps);
+    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready[1]), kEpiWarps);
     ptx::mbar_init(ptx::smem_u32(&ctl.drain), 1);
     ctl.abort_flag = 0;
     ptx::fence_mbar_init();
@@ -357,7 +452,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
-      const int b = item.b, n_pad = g->n_pad, nb = n_pad / kBM, bn = g->bn, t_f = g->t_f;
+      const int b = item.b, n_pad = g->n_pad, nb = n_pad / kBM, bn = g->bn, steps = g->t_f + g->energy_pass;
       const void* tmJ = &g->tmJ;
       const void* tmS = &g->tmS;
       const uint32_t* gflags = g->flags;
@@ -374,7 +469,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       }
       __syncwarp();
       const int pre = KB < kStages ? KB : kStages;
-      for (int t = 0; t < t_f && ok; ++t) {
+      for (int t = 0; t < steps && ok; ++t) {
         const int sy = (t & 1) * bn;
         const uint32_t claim_stage = stage;
         int claimed = 0;
@@ -451,12 +546,13 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcGroup* g = groups + items[w].group;
-      const int KB = g->n_pad / kBK, t_f = g->t_f;
+      const int KB = g->n_pad / kBK, steps = g->t_f + g->energy_pass;
       const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
-      for (int t = 0; t < t_f && ok; ++t, ++gstep) {
+      for (int t = 0; t < steps && ok; ++t, ++gstep) {
         // the epilogue has written this step's bias (h + sigma z d) into the
         // accumulator the step uses; the product accumulates onto it
-        ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.bias_ready), gstep & 1u, &ctl, status));
+        ok = __all_sync(0xffffffffu,
+                        wait_bar(ptx::smem_u32(&ctl.bias_ready[gstep & 1u]), (gstep >> 1) & 1u, &ctl, status));
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
@@ -605,8 +701,11 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
     flags += static_cast<size_t>(groups) * nb;
     state += static_cast<size_t>(groups) * 2 * bn * jobs[j].pb.n_pad * 2;
   }
+  // cleared every launch: epoch flags, then per group one done-counter and bn 2H sums
+  const size_t cleared = align_up(flags * 4, 256) + align_up(ngroups * 4, 256) +
+                         align_up(ngroups * static_cast<size_t>(jobs[0].bn) * 8, 256);
   *bytes = static_cast<int64_t>(align_up(ngroups * sizeof(TcGroup), 256) + align_up(nitems * sizeof(TcItem), 256) +
-                                align_up((static_cast<size_t>(capacity) + 1) * 4, 256) + align_up(flags * 4, 256) + state);
+                                align_up((static_cast<size_t>(capacity) + 1) * 4, 256) + cleared + state);
   return NMFA_OK;
 }
 
@@ -627,8 +726,9 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   for (int j = 0; j < count; ++j) {
     const int bn = jobs[j].bn, nb = jobs[j].pb.n_pad / kBM;
     const int groups = (jobs[j].rp.replicas + bn - 1) / bn;
+    const int steps = jobs[j].rp.t_f + (tc_fuses_energy(jobs[j].pb, jobs[j].rp) ? 1 : 0);
     for (int c = 0; c < groups; ++c) {
-      gl.push_back({j, c, nb, static_cast<double>(jobs[j].rp.t_f) * (2.0 * nb + 8.0)});
+      gl.push_back({j, c, nb, static_cast<double>(steps) * (2.0 * nb + 8.0)});
       nitems += nb;
       nflags += nb;
     }
@@ -637,7 +737,9 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   const size_t off_items = align_up(gl.size() * sizeof(TcGroup), 256);
   const size_t off_first = off_items + align_up(nitems * sizeof(TcItem), 256);
   const size_t off_flags = off_first + align_up((static_cast<size_t>(capacity) + 1) * 4, 256);
-  const size_t off_state = off_flags + align_up(nflags * 4, 256);
+  const size_t off_done = off_flags + align_up(nflags * 4, 256);
+  const size_t off_e2h = off_done + align_up(gl.size() * 4, 256);
+  const size_t off_state = off_e2h + align_up(gl.size() * static_cast<size_t>(jobs[0].bn) * 8, 256);
   // group descriptors
   plan->host.assign(off_flags, 0);
   TcGroup* hg = reinterpret_cast<TcGroup*>(plan->host.data());
@@ -668,6 +770,11 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     g.stream = jb.rp.stream_id;
     g.flags = reinterpret_cast<uint32_t*>(base + off_flags) + flag_pos;
     flag_pos += gl[k].nb;
+    g.energy_pass = tc_fuses_energy(jb.pb, jb.rp) ? 1 : 0;
+    g.e_done = reinterpret_cast<uint32_t*>(base + off_done) + k;
+    g.e2h = reinterpret_cast<int64_t*>(base + off_e2h) + k * static_cast<size_t>(bn);
+    g.energy = g.energy_pass ? jb.rp.energy : nullptr;
+    g.energy_i64 = g.energy_pass ? jb.rp.energy_i64 : nullptr;
     g.S16 = reinterpret_cast<__nv_bfloat16*>(base + state_pos);
     state_pos += static_cast<size_t>(2) * bn * g.n_pad * 2;
     if ((rc = make_map_bf16(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad, kBM))) return rc;
@@ -707,7 +814,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   plan->items_off = off_items;
   plan->first_off = off_first;
   plan->flags_off = off_flags;
-  plan->flags_bytes = nflags * 4;
+  plan->flags_bytes = off_state - off_flags;  // flags, done counters and 2H sums
   plan->grid = grid;
   plan->bn = jobs[0].bn;
   plan->status = status;

@@ -49,6 +49,9 @@ struct nmfa_problem {
   bool csr = false;
   bool integer_valued = false;
   bool int8_ok = false;  // integer problem with |J| <= 127: int8 energy copy
+  // integer problem with max_i (sum_j |J_ij| + 2 |h_i|) < 2^24: the tensor kernel
+  // forms the energies exactly in its own epilogue
+  bool energy_exact = false;
   int32_t nnz = 0;
   int32_t n_pad = 0;
   int device = 0;
@@ -233,10 +236,13 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
   if (rc) return rc;
   if (J == nullptr) return set_error(NMFA_EINVAL, "J is NULL");
   bool integer = true, int8_ok = true, bf16_ok = true, e4m3_ok = true;
+  double max_row = 0.0;  // max_i (sum_j |J_ij| + 2 |h_i|)
   for (int32_t i = 0; i < n; ++i) {
+    double row = 0.0;
     if (h != nullptr) {
       if (!std::isfinite(h[i])) return set_error(NMFA_EINVAL, "h has a non-finite entry");
       if (h[i] != std::nearbyint(h[i]) || std::fabs(h[i]) >= 2147483648.0) integer = false;
+      row = 2.0 * std::fabs(h[i]);
     }
     if (J[static_cast<int64_t>(i) * n + i] != 0.0) return set_error(NMFA_EDIAG, "J has a nonzero diagonal entry");
     for (int32_t j = 0; j < n; ++j) {
@@ -245,7 +251,9 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
       if (j > i && v != J[static_cast<int64_t>(j) * n + i]) return set_error(NMFA_ENOTSYM, "J is not symmetric");
       if (v != std::nearbyint(v) || std::fabs(v) >= 2147483648.0) integer = false;
       if (std::fabs(v) > 127.0) int8_ok = false;
+      row += std::fabs(v);
     }
+    max_row = std::max(max_row, row);
   }
   int8_ok = int8_ok && integer && static_cast<int64_t>(n) * 127 < (1ll << 30);
   if (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) {
@@ -264,6 +272,7 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
   p->precision = precision;
   p->integer_valued = integer;
   p->int8_ok = int8_ok;
+  p->energy_exact = integer && max_row < 16777216.0;
   p->n_pad = (n + 127) / 128 * 128;
   cudaStream_t st = nullptr;
   auto fail = [&](int code) {
@@ -467,6 +476,9 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
   rp.s_out = s_out_dev;
   rp.phi_out = phi_out_dev;
   rp.signs = signs_dev;
+  rp.energy = energy_dev;
+  rp.energy_i64 = energy_i64_dev;
+  bool energy_fused = false;
   if (p->profiling && (rc = cuda_error(cudaEventRecord(p->prof0, st), "profile event"))) return rc;
   switch (p->precision) {
     case NMFA_FP64:
@@ -509,6 +521,8 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
       pb.fp8 = false;
       pb.inv_d32 = p->inv_d32;
       pb.h32 = p->h32;
+      pb.energy_exact = p->energy_exact;
+      energy_fused = tc_fuses_energy(pb, rp);
       int64_t bytes = 0;
       if ((rc = tc_workspace_bytes(pb, replicas, &bytes))) return rc;
       // FP8-stored couplings are expanded to BF16 in front of the kernel's scratch
@@ -531,7 +545,7 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
     if ((rc = cuda_error(cudaEventRecord(p->prof1, st), "profile event"))) return rc;
     p->prof_valid = true;
   }
-  if (energy_dev != nullptr || energy_i64_dev != nullptr) {
+  if (!energy_fused && (energy_dev != nullptr || energy_i64_dev != nullptr)) {
     EnergyProblem ep{};
     ep.n = p->n;
     ep.J8 = p->J8;
@@ -641,6 +655,8 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
   rp.stream_id = stream_id;
   rp.noise_sign = 1;
   rp.signs = signs_dev;
+  rp.energy = energy_dev;
+  rp.energy_i64 = energy_i64_dev;
   TcProblem pb{};
   pb.n = p->n;
   pb.n_pad = p->n_pad;
@@ -648,8 +664,9 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
   pb.fp8 = false;
   pb.inv_d32 = p->inv_d32;
   pb.h32 = p->h32;
+  pb.energy_exact = p->energy_exact;
   if ((rc = launch_tc_static_scratch(pb, rp, p->status, st))) return rc;
-  if (energy_dev != nullptr || energy_i64_dev != nullptr) {
+  if (!tc_fuses_energy(pb, rp) && (energy_dev != nullptr || energy_i64_dev != nullptr)) {
     EnergyProblem ep{};
     ep.n = p->n;
     ep.J8 = p->J8;
@@ -674,6 +691,7 @@ struct nmfa_batch {
   std::vector<std::pair<int, size_t>> expand;  // (job, offset into jexp)
   DevBuf signs;             // sign scratch for jobs that did not supply a buffer
   std::vector<int8_t*> signs_ptr;
+  std::vector<char> energy_fused;  // per job: energies formed inside the persistent kernel
   int32_t* status = nullptr;
   std::vector<TcPlan> plans;  // one persistent launch per tile width in the batch
   cudaStream_t own = nullptr;
@@ -713,7 +731,7 @@ static int batch_enqueue(nmfa_batch* b, cudaStream_t st) {
     if ((rc = tc_enqueue_plan(plan, false, st))) return rc;
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     const nmfa_job& jb = b->jobs[j];
-    if (jb.energy_dev == nullptr && jb.energy_i64_dev == nullptr) continue;
+    if (b->energy_fused[j] || (jb.energy_dev == nullptr && jb.energy_i64_dev == nullptr)) continue;
     nmfa_problem* p = b->problems[j];
     EnergyProblem ep{};
     ep.n = p->n;
@@ -792,6 +810,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.pb.fp8 = false;
     t.pb.inv_d32 = p->inv_d32;
     t.pb.h32 = p->h32;
+    t.pb.energy_exact = p->energy_exact;
     t.rp = RunParams{};
     t.rp.T = jb.T_dev;
     t.rp.t_f = jb.t_f;
@@ -802,6 +821,9 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.rp.stream_id = jb.stream_id;
     t.rp.noise_sign = 1;
     t.rp.signs = sg;
+    t.rp.energy = jb.energy_dev;
+    t.rp.energy_i64 = jb.energy_i64_dev;
+    b->energy_fused.push_back(tc_fuses_energy(t.pb, t.rp) ? 1 : 0);
     t.bn = (options & NMFA_BATCH_BN64) ? 64
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
                                              : tc_pick_bn(jb.replicas);

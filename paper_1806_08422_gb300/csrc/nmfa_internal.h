@@ -36,6 +36,11 @@ struct RunParams {
   double* s_out;          // device R*n or nullptr
   double* phi_out;        // device R*n or nullptr
   int8_t* signs;          // device R*n (always present: the library supplies scratch)
+  // Energies of the sign vectors (Eq. 1), device R, or nullptr.  The tensor path
+  // computes them inside its persistent kernel when the problem allows it exactly
+  // (TcProblem::energy_exact); every other path leaves them to launch_energy.
+  double* energy;
+  int64_t* energy_i64;
 };
 
 // ---- CUDA-core dense path (FP32 / FP64) -----------------------------------
@@ -105,7 +110,15 @@ struct TcProblem {
   bool fp8;
   const float* inv_d32;   // n_pad, 0 in padding
   const float* h32;       // h_i in binary32, n_pad (0 in padding)
+  // Integer J and h with max_i (sum_j |J_ij| + 2 |h_i|) < 2^24: the product J s~ + 2h
+  // of a sign vector is exact in the FP32 accumulator, so the kernel can form the
+  // energies itself.
+  bool energy_exact;
 };
+// True when the tensor kernel forms this run's energies (no separate energy launch).
+inline bool tc_fuses_energy(const TcProblem& pb, const RunParams& rp) {
+  return pb.energy_exact && rp.t_f > 0 && (rp.energy != nullptr || rp.energy_i64 != nullptr);
+}
 struct TcWorkspace {
   void* S16;              // bf16 [2][r_pad][n_pad]
   uint32_t* flags;        // [row blocks][replica blocks]
