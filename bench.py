@@ -102,10 +102,28 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(sample_replicas=16, sample_steps=200, nthreads=0):
+def kernel_traffic():
+    """DRAM bytes per launch of the tensor kernel from the committed ncu capture of the
+    bench workload, or None when the kernel sources have changed since the capture."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "nmfa_tc_kernel_sk2000_r1024_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for p in rec["sources"]:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+    except Exception:
+        return None
+
+
+def cpu_baseline(sample_replicas=48, sample_steps=T_F, nthreads=0):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the same
-    instance and schedule, `sample_replicas` replicas over the first `sample_steps`
-    steps, OpenMP over replicas on every host core."""
+    instance and schedule, `sample_replicas` of the 1024 replicas over the first
+    `sample_steps` steps (about 10 s of CPU work at the defaults), OpenMP over
+    replicas on every host core."""
     import numpy as np
 
     import oracle
@@ -132,18 +150,18 @@ def run_reference(args):
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(sample_replicas=16, sample_steps=50))
+        vals.append(cpu_baseline(sample_replicas=16, sample_steps=200))
     wall = time.perf_counter() - t_all
-    units = sum(16 * N_SPINS * 50 for _ in vals)
+    units = sum(16 * N_SPINS * 200 for _ in vals)
     value = units / wall
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "SK N=2000 +-1, h=0, sigma=alpha=0.15, default schedule; each step a bounded "
-                                   "sample: 16 replicas x 50 steps of the 1024-replica, 1000-step run"},
+                                   "sample: 16 replicas x 200 steps of the 1024-replica, 1000-step run"},
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "16 replicas x 50 steps per bench step"},
+                             "sample": "16 replicas x 200 steps per bench step"},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -255,7 +273,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         achieved = flops / (kern_ms / 1e3) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": kernel_traffic() if args.tf == T_F else None,
                     "kernel": "nmfa_tc_kernel<128>", "kernel_ms": kern_ms,
                     "peak_source": "%s bf16_tflops_sustained" % peak_kind}
     else:
