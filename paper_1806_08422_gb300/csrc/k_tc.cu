@@ -4,8 +4,8 @@
 // The coupling product of line 6 over all replicas is the GEMM P = J S (J: n x n,
 // S: n x R); CTA (b, c) owns the output tile of spins [128 b, 128 b + 128) and
 // replicas [BN c, BN c + BN) for the whole run:
-//   - warp 0 streams 64-wide K slices of J's row block and of S's replica block
-//     into a STAGES-deep shared-memory ring with TMA (128-byte swizzle); the J
+//   - warp 0 streams 128-deep K slices of J's row block and of S's replica block
+//     into a 3-slot shared-memory ring with TMA (128-byte swizzle); the J
 //     slices of a step start before the step's state is published, the S slices
 //     after the whole warp has seen every row block's epoch flag of the replica
 //     block reach the step;
@@ -47,7 +47,7 @@ namespace nmfa {
 namespace {
 
 constexpr int kBM = 128;               // spins per tile (TMEM lanes)
-constexpr int kBK = 64;                // K slice: 64 BF16 = one 128-byte swizzle row
+constexpr int kBK = 64;                // K atom: 64 BF16 = one 128-byte swizzle row
 constexpr int kBNMax = 128;            // replicas per tile (MMA N), 64 or 128 per group
 // Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
 // tile of BN replicas takes BN / 8 warps (16 for 128-replica tiles, 8 for 64).
@@ -57,9 +57,18 @@ struct TcShape {
   static constexpr int kThreads = 64 + 32 * kEpiWarps;
 };
 constexpr int kColsPerWarp = 32;
-constexpr int kStages = 6;
-constexpr uint32_t kABytes = kBM * 128;
-constexpr uint32_t kStageBytes = kABytes + kBNMax * 128;
+// Ring slots of a 128-deep K slice (two swizzle atoms): eight MMAs per slot.  An
+// M = 128, N <= 128 tcgen05.mma costs its issuing warp about as long as its own tensor
+// work, so the handshake per slot (full-barrier wait, commit) is amortised over
+// eight MMAs rather than four (measured on GB300 with the noise draws running: ~77
+// instead of ~101 clocks per MMA against 64 of tensor work).  Slot layout:
+// [A atom 0][A atom 1][B atom 0][B atom 1].
+constexpr int kAtoms = 2;
+constexpr int kKSlot = kAtoms * kBK;
+constexpr int kStages = 3;
+constexpr uint32_t kABytes = kBM * 128;         // one A (J) atom: 128 rows x 128 bytes
+constexpr uint32_t kBAtomBytes = kBNMax * 128;  // one B (S) atom slot: up to 128 rows x 128 bytes
+constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
 // TMEM columns: two accumulators [0, 128) and [128, 256) (step g uses g % 2),
 // FP32 master state [256, 384).
 constexpr uint32_t kTmemCols = 512;
@@ -463,11 +472,11 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       const void* tmJ = &g->tmJ;
       const void* tmS = &g->tmS;
       const uint32_t* gflags = g->flags;
-      const uint32_t stage_tx = kABytes + static_cast<uint32_t>(bn) * 128u;
-      const int KB = n_pad / kBK;
-      // every row block starts its K sweep at a different slice (2 b) to spread the
+      const uint32_t stage_tx = kAtoms * (kABytes + static_cast<uint32_t>(bn) * 128u);
+      const int KB = n_pad / kKSlot;  // ring slots per step (= row blocks)
+      // every row block starts its K sweep at its own 128-deep slice (b) to spread the
       // CTAs' reads of J and S over L2
-      const int kslice_base = (2 * b) % KB;
+      const int kslice_base = b % KB;
       if (lane == 0) {
         acquire_tensormap(tmJ);
         acquire_tensormap(tmS);
@@ -485,7 +494,10 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
           ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-          ptx::tma_load_2d_warp(ring + stage * kStageBytes, tmJ, ks * kBK, b * kBM, full0 + 8u * stage);
+#pragma unroll
+          for (int a = 0; a < kAtoms; ++a)
+            ptx::tma_load_2d_warp(ring + stage * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM,
+                                  full0 + 8u * stage);
           ++claimed;
           ++filled;
           if (++stage == kStages) {
@@ -506,7 +518,10 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
           uint32_t st = claim_stage;
           int ks2 = kslice_base;
           for (int kb = 0; kb < claimed; ++kb) {
-            ptx::tma_load_2d_warp(ring + st * kStageBytes + kABytes, tmS, ks2 * kBK, sy, full0 + 8u * st);
+#pragma unroll
+            for (int a = 0; a < kAtoms; ++a)
+              ptx::tma_load_2d_warp(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
+                                    ks2 * kKSlot + a * kBK, sy, full0 + 8u * st);
             if (++st == kStages) st = 0;
             if (++ks2 == KB) ks2 = 0;
           }
@@ -517,8 +532,12 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
           if (!ok) break;
           const uint32_t sA = ring + stage * kStageBytes;
           ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-          ptx::tma_load_2d_warp(sA, tmJ, ks * kBK, b * kBM, full0 + 8u * stage);
-          ptx::tma_load_2d_warp(sA + kABytes, tmS, ks * kBK, sy, full0 + 8u * stage);
+#pragma unroll
+          for (int a = 0; a < kAtoms; ++a) {
+            ptx::tma_load_2d_warp(sA + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, full0 + 8u * stage);
+            ptx::tma_load_2d_warp(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy,
+                                  full0 + 8u * stage);
+          }
           ++filled;
           if (++stage == kStages) {
             stage = 0;
@@ -543,17 +562,18 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     // The whole warp runs the loop and one elected lane issues each tcgen05.mma and
     // commit.  The ring position is carried as (stage, phase) counters and the
     // shared-memory descriptors are formed once and advanced by adding to their
-    // start-address field (32 bytes per K = 16 step, one stage per ring slot; the
+    // start-address field (32 bytes per K = 16 step, one atom or slot further on; the
     // field cannot carry out of its 14 bits because shared addresses stay below 256 KB).
     uint32_t stage = 0, phase = 0, gstep = 0;
     bool ok = true;
     bool issued = false;
     const uint64_t desc0 = ptx::sw128_desc(ring);
-    constexpr uint64_t kDescStage = kStageBytes >> 4, kDescB = kABytes >> 4, kDescK = 32 >> 4;
+    constexpr uint64_t kDescStage = kStageBytes >> 4, kDescA = kABytes >> 4, kDescB = (kAtoms * kABytes) >> 4,
+                       kDescBAtom = kBAtomBytes >> 4, kDescK = 32 >> 4;
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcGroup* g = groups + items[w].group;
-      const int KB = g->n_pad / kBK, steps = g->t_f + g->energy_pass;
+      const int KB = g->n_pad / kKSlot, steps = g->t_f + g->energy_pass;
       const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
       for (int t = 0; t < steps && ok; ++t, ++gstep) {
         // the epilogue has written this step's bias (h + sigma z d) into the
@@ -569,8 +589,11 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
           if (!ok) break;
           const uint64_t da = desc0 + kDescStage * stage;
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            ptx::mma_bf16_warp(acc, da + kDescK * kk, da + kDescB + kDescK * kk, idesc);
+          for (int a = 0; a < kAtoms; ++a) {
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              ptx::mma_bf16_warp(acc, da + kDescA * a + kDescK * kk, da + kDescB + kDescBAtom * a + kDescK * kk, idesc);
+            }
           }
           issued = true;
           ptx::mma_commit_warp(empty0 + 8u * stage);
