@@ -48,14 +48,6 @@ namespace {
 
 constexpr int kBM = 128;               // spins per tile (TMEM lanes)
 constexpr int kBK = 64;                // K atom: 64 BF16 = one 128-byte swizzle row
-constexpr int kBNMax = 128;            // replicas per tile (MMA N), 64 or 128 per group
-// Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
-// tile of BN replicas takes BN / 8 warps (16 for 128-replica tiles, 8 for 64).
-template <int BN>
-struct TcShape {
-  static constexpr int kEpiWarps = BN / 8;
-  static constexpr int kThreads = 64 + 32 * kEpiWarps;
-};
 constexpr int kColsPerWarp = 32;
 // Ring slots of a 128-deep K slice (two swizzle atoms): eight MMAs per slot.  An
 // M = 128, N <= 128 tcgen05.mma costs its issuing warp about as long as its own tensor
@@ -65,16 +57,34 @@ constexpr int kColsPerWarp = 32;
 // [A atom 0][A atom 1][B atom 0][B atom 1].
 constexpr int kAtoms = 2;
 constexpr int kKSlot = kAtoms * kBK;
-constexpr int kStages = 3;
-constexpr uint32_t kABytes = kBM * 128;         // one A (J) atom: 128 rows x 128 bytes
-constexpr uint32_t kBAtomBytes = kBNMax * 128;  // one B (S) atom slot: up to 128 rows x 128 bytes
-constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
-// TMEM columns: two accumulators [0, 128) and [128, 256) (step g uses g % 2),
-// FP32 master state [256, 384).
-constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAcc1 = kBNMax;
-constexpr uint32_t kColMaster = 2 * kBNMax;
-constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
+// Geometry per tile width BN (replicas per tile, the MMA's N: 64 or 128).
+//   Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
+//   tile takes BN / 8 of them (16 for 128-replica tiles, 8 for 64).
+//   One CTA per SM (a kernel that allocates TMEM is given one CTA per SM by the
+//   occupancy rules, which the cooperative launch follows), with the ring filling
+//   the shared memory: 3 slots of 64 KB for 128-replica tiles, 4 of 48 KB for 64.
+//   TMEM columns: accumulators [0, BN) and [BN, 2 BN) (step g uses g % 2), FP32
+//   master state [2 BN, 3 BN).
+template <int BN>
+struct TcShape {
+  static constexpr int kEpiWarps = BN / 8;
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+  // register budget handed to the compiler (launch bound): the 64-replica kernel fits
+  // 96 registers without spills when asked for two blocks' worth, and spills a little
+  // at the 168 it takes when left free (it still runs one CTA per SM)
+  static constexpr int kRegBlocks = BN == 64 ? 2 : 1;
+  static constexpr int kStages = BN == 64 ? 4 : 3;
+  static constexpr uint32_t kBAtomBytes = BN * 128;  // one B (S) atom: BN rows x 128 bytes
+  static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
+  static constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
+  static constexpr uint32_t kTmemCols = 512;
+  static constexpr uint32_t kColAcc1 = BN;
+  static constexpr uint32_t kColMaster = 2 * BN;
+  static_assert(kStages <= kMaxStages, "ring slots");
+  static_assert(3 * BN <= kTmemCols, "TMEM columns");
+};
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A CTA that reaches a new group early waits for the group's other CTAs to finish
 // the groups scheduled before it; that first wait gets a longer bound.
@@ -108,8 +118,8 @@ struct TcItem {
 };
 
 struct SharedCtl {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
   uint64_t acc_full;
   // The step's accumulator holds its bias (epilogue -> MMA).  Step g uses
   // bias_ready[g % 2]: every epilogue warp arrives for step g + 1 before it waits for
@@ -180,10 +190,11 @@ __device__ __forceinline__ void acquire_tensormap(const void* m) {
 // (A) the bias of one step, h_i + sigma z d_i, written into the accumulator the step
 // will use (the Gaussian draws do not depend on the state, so this runs while the
 // tensor core still computes the previous step), then signalled to the MMA issuer.
+template <int BN>
 __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base, int col0, int rbase, int i,
                                            uint32_t stream, const RoundKeys& rk, float sigma_ns, float dd, float hi,
                                            int lane, SharedCtl* ctl) {
-  const uint32_t acc = lane_base + ((g & 1u) ? kColAcc1 : 0u);
+  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll 1
   for (int cc = 0; cc < kColsPerWarp; cc += 16) {
@@ -206,9 +217,10 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
 }
 
 // (A') the accumulator start of the energy product: 2 h_i, no noise.
+template <int BN>
 __device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base, int col0, float hi, int lane,
                                                   SharedCtl* ctl) {
-  const uint32_t acc = lane_base + ((g & 1u) ? kColAcc1 : 0u);
+  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __float_as_uint(2.0f * hi);
@@ -282,6 +294,7 @@ template <int BN>
 __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
                                               SharedCtl* ctl, int32_t* status, uint32_t& gstep) {
   constexpr int kCW = kColsPerWarp;
+  constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1, kColMaster = TcShape<BN>::kColMaster;
   const int q = (e + 2) & 3;
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
   const int n = g->n, n_pad = g->n_pad, t_f = g->t_f, R = g->replicas;
@@ -332,7 +345,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   const float sc = inv_d > 0.0f ? inv_d : 1.0f;
   // (A) the bias of step t: the Gaussian draws do not depend on the state, so they
   // are generated while the tensor core still computes the previous step
-  if (t_f > 0) write_bias(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+  if (t_f > 0) write_bias<BN>(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
 
   for (int t = 0; t < t_f; ++t, ++gstep) {
     float inv_T = 0.0f;
@@ -341,9 +354,9 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     __nv_bfloat16* Snext = S16 + static_cast<size_t>((t + 1) & 1) * plane;
     // the next step's bias goes into the other accumulator (read last two steps ago)
     if (t + 1 < t_f)
-      write_bias(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+      write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
     else if (energy_pass)
-      write_energy_bias(gstep + 1, lane_base, col0, hi, lane, ctl);
+      write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
     ptx::tc_fence_after();
@@ -422,10 +435,13 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
 }
 
 template <int BN>
-__global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
+__global__ void __launch_bounds__(TcShape<BN>::kThreads, TcShape<BN>::kRegBlocks)
 nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
                int32_t* status) {
   constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
+  constexpr int kStages = TcShape<BN>::kStages;
+  constexpr uint32_t kStageBytes = TcShape<BN>::kStageBytes, kBAtomBytes = TcShape<BN>::kBAtomBytes;
+  constexpr uint32_t kTmemCols = TcShape<BN>::kTmemCols, kColAcc1 = TcShape<BN>::kColAcc1;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   __shared__ SharedCtl ctl;
 
@@ -446,7 +462,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(&ctl.tmem_slot), kTmemCols);
+    ptx::tmem_alloc<kTmemCols>(ptx::smem_u32(&ctl.tmem_slot));
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -629,7 +645,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
+    ptx::tmem_dealloc<kTmemCols>(tmem);
   }
 }
 
@@ -681,16 +697,19 @@ int co_resident_ctas_bn(int* capacity) {
   if (cached < 0) {
     int rc;
     if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(kSmemBytes)),
+                                              static_cast<int>(TcShape<BN>::kSmemBytes)),
                          "tensor kernel attribute")))
       return rc;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN>,
-                                                                       TcShape<BN>::kThreads, kSmemBytes),
+                                                                       TcShape<BN>::kThreads,
+                                                                       TcShape<BN>::kSmemBytes),
                          "occupancy")))
       return rc;
+    // never more CTAs on an SM than its TMEM holds (each allocates kTmemCols of 512)
+    per_sm = std::min(per_sm, static_cast<int>(512 / TcShape<BN>::kTmemCols));
     cached = per_sm * sms;
   }
   *capacity = cached;
@@ -874,7 +893,7 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.grid, 1, 1);
   cfg.blockDim = dim3(plan.bn == 64 ? TcShape<64>::kThreads : TcShape<128>::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.dynamicSmemBytes = plan.bn == 64 ? TcShape<64>::kSmemBytes : TcShape<128>::kSmemBytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
