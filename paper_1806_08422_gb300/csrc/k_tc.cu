@@ -62,29 +62,34 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 // Geometry per tile width BN (replicas per tile, the MMA's N: 64 or 128).
 //   Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
 //   tile takes BN / 8 of them (16 for 128-replica tiles, 8 for 64).
-//   One CTA per SM (a kernel that allocates TMEM is given one CTA per SM by the
-//   occupancy rules, which the cooperative launch follows), with the ring filling
-//   the shared memory: 3 slots of 64 KB for 128-replica tiles, 4 of 48 KB for 64.
-//   TMEM columns: accumulators [0, BN) and [BN, 2 BN) (step g uses g % 2), FP32
-//   master state [2 BN, 3 BN).
+//   One CTA per SM: a kernel that allocates TMEM is given one CTA per SM by the
+//   occupancy rules, which the cooperative launch follows.  A 128-replica CTA runs
+//   one tile pipeline (TMA warp, MMA warp, 16 epilogue warps) with a ring of 3
+//   slots of 64 KB.  A 64-replica CTA runs two independent pipelines (2 x 10 warps),
+//   each with its own ring of 2 slots of 48 KB, barriers, work list and half of
+//   the TMEM: a 64-replica tile's products are short, and the second pipeline's
+//   MMAs fill the time the first spends in its epilogue and state exchange.
+//   TMEM columns of a pipeline (from its base): accumulators [0, BN) and
+//   [BN, 2 BN) (step g uses g % 2), FP32 master state [2 BN, 3 BN).
 template <int BN>
 struct TcShape {
   static constexpr int kEpiWarps = BN / 8;
-  static constexpr int kThreads = 64 + 32 * kEpiWarps;
-  // register budget handed to the compiler (launch bound): the 64-replica kernel fits
-  // 96 registers without spills when asked for two blocks' worth, and spills a little
-  // at the 168 it takes when left free (it still runs one CTA per SM)
-  static constexpr int kRegBlocks = BN == 64 ? 2 : 1;
-  static constexpr int kStages = BN == 64 ? 4 : 3;
+  static constexpr int kSubs = BN == 64 ? 2 : 1;   // tile pipelines per CTA
+  static constexpr int kSubWarps = 2 + kEpiWarps;  // warps per pipeline
+  static constexpr int kThreads = 32 * kSubWarps * kSubs;
+  static constexpr int kStages = BN == 64 ? 2 : 3;  // ring slots per pipeline
   static constexpr uint32_t kBAtomBytes = BN * 128;  // one B (S) atom: BN rows x 128 bytes
   static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
-  static constexpr size_t kSmemBytes = static_cast<size_t>(kStages) * kStageBytes + 1024;
-  static constexpr uint32_t kTmemCols = 512;
+  static constexpr uint32_t kRingBytes = kStages * kStageBytes;
+  static constexpr size_t kSmemBytes = static_cast<size_t>(kSubs) * kRingBytes + 1024;
+  static constexpr uint32_t kTmemCols = 512;  // allocated once per CTA
+  static constexpr uint32_t kSubCols = kTmemCols / kSubs;
   static constexpr uint32_t kColAcc1 = BN;
   static constexpr uint32_t kColMaster = 2 * BN;
   static_assert(kStages <= kMaxStages, "ring slots");
-  static_assert(3 * BN <= kTmemCols, "TMEM columns");
+  static_assert(3 * BN <= kSubCols, "TMEM columns");
 };
+constexpr int kMaxSubs = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A CTA that reaches a new group early waits for the group's other CTAs to finish
 // the groups scheduled before it; that first wait gets a longer bound.
@@ -286,16 +291,17 @@ __device__ __noinline__ void energy_readout(const TcGroup* __restrict__ g, uint3
 }
 
 // Epilogue warps' work for one item (one 128-spin tile of one group), from the
-// initial state through t_f steps to the readout.  Warp e serves TMEM lane quarter
-// q = (e + 2) % 4 (spins 32q..32q+31 of the tile) and column group e / 4 (32
-// replicas), 16 columns per tcgen05.ld.  `gstep` counts the CTA's steps across items
+// initial state through t_f steps to the readout.  Epilogue warp e of a pipeline is
+// physical warp e + QOFF (mod 4), which may access TMEM lane quarter
+// q = (e + QOFF) % 4 (spins 32q..32q+31 of the tile); it serves that quarter and
+// column group e / 4 (32 replicas), 16 columns per tcgen05.ld.  `gstep` counts the CTA's steps across items
 // (the parity of the accumulator barriers).  Returns false on abort.
-template <int BN>
+template <int BN, int QOFF>
 __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
                                               SharedCtl* ctl, int32_t* status, uint32_t& gstep) {
   constexpr int kCW = kColsPerWarp;
   constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1, kColMaster = TcShape<BN>::kColMaster;
-  const int q = (e + 2) & 3;
+  const int q = (e + QOFF) & 3;
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
   const int n = g->n, n_pad = g->n_pad, t_f = g->t_f, R = g->replicas;
   const int col0 = (e >> 2) * kCW;
@@ -434,43 +440,27 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   return true;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(TcShape<BN>::kThreads, TcShape<BN>::kRegBlocks)
-nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
-               int32_t* status) {
+// One tile pipeline of the persistent kernel: its TMA warp (lw 0), MMA warp (lw 1) and
+// epilogue warps (lw 2..), its control block, ring slots, TMEM columns and work list
+// (plan slot SUB * gridDim.x + blockIdx.x).  SUB is a template argument so that the
+// control block's shared-memory address stays a constant.
+template <int BN, int SUB>
+__device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items,
+                                             const int32_t* __restrict__ first, int32_t* status, SharedCtl* ctl_all,
+                                             uint32_t ring_base, uint32_t tmem_base, int warp, int lane) {
   constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
+  constexpr int kSubWarps = TcShape<BN>::kSubWarps;
   constexpr int kStages = TcShape<BN>::kStages;
   constexpr uint32_t kStageBytes = TcShape<BN>::kStageBytes, kBAtomBytes = TcShape<BN>::kBAtomBytes;
-  constexpr uint32_t kTmemCols = TcShape<BN>::kTmemCols, kColAcc1 = TcShape<BN>::kColAcc1;
-  extern __shared__ __align__(1024) uint8_t smem_dyn[];
-  __shared__ SharedCtl ctl;
+  constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1;
+  SharedCtl& ctl = ctl_all[SUB];
+  const int lw = warp - SUB * kSubWarps;
+  const int slot = SUB * static_cast<int>(gridDim.x) + static_cast<int>(blockIdx.x);
+  const int w_begin = first[slot], w_end = first[slot + 1];
+  const uint32_t ring = ring_base + static_cast<uint32_t>(SUB) * TcShape<BN>::kRingBytes;
+  const uint32_t tmem = tmem_base + static_cast<uint32_t>(SUB) * TcShape<BN>::kSubCols;
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w_begin = first[blockIdx.x], w_end = first[blockIdx.x + 1];
-  const uint32_t ring = (ptx::smem_u32(smem_dyn) + 1023u) & ~1023u;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(ptx::smem_u32(&ctl.full[s]), 1);
-      ptx::mbar_init(ptx::smem_u32(&ctl.empty[s]), 1);
-    }
-    ptx::mbar_init(ptx::smem_u32(&ctl.acc_full), 1);
-    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready[0]), kEpiWarps);
-    ptx::mbar_init(ptx::smem_u32(&ctl.bias_ready[1]), kEpiWarps);
-    ptx::mbar_init(ptx::smem_u32(&ctl.drain), 1);
-    ctl.abort_flag = 0;
-    ptx::fence_mbar_init();
-  }
-  if (warp == 1) {
-    ptx::tmem_alloc<kTmemCols>(ptx::smem_u32(&ctl.tmem_slot));
-    ptx::tmem_relinquish();
-  }
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::tc_fence_after();
-  const uint32_t tmem = ctl.tmem_slot;
-
-  if (warp == 0) {
+  if (lw == 0) {
     // ------------------------------------------------------------ TMA producer
     // Per step: claim the first ring slots and start their J slices at once (J
     // does not depend on the previous step), wait with the whole warp until every
@@ -573,7 +563,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (lw == 1) {
     // ------------------------------------------------------------ MMA issuer
     // The whole warp runs the loop and one elected lane issues each tcgen05.mma and
     // commit.  The ring position is carried as (stage, phase) counters and the
@@ -631,21 +621,73 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int e = warp - 2;
+    // epilogue warp e (physical warp e + 2 + SUB * kSubWarps) serves column group
+    // e / 4 and the TMEM lane quarter that warp may access; over the pipeline's
+    // warps each (quarter, column group) pair occurs once
+    const int e = lw - 2;
     uint32_t gstep = 0;
     bool ok = true;
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
-      ok = epilogue_item<BN>(g, item.b, e, lane, tmem, &ctl, status, gstep);
+      ok = epilogue_item<BN, (2 + SUB * kSubWarps) & 3>(g, item.b, e, lane, tmem, &ctl, status, gstep);
     }
+  }
+
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
+nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
+               int32_t* status) {
+  constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
+  constexpr int kSubs = TcShape<BN>::kSubs, kSubWarps = TcShape<BN>::kSubWarps;
+  constexpr int kStages = TcShape<BN>::kStages;
+  constexpr uint32_t kTmemCols = TcShape<BN>::kTmemCols;
+  extern __shared__ __align__(1024) uint8_t smem_dyn[];
+  __shared__ SharedCtl ctl_all[kSubs];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ring_base = (ptx::smem_u32(smem_dyn) + 1023u) & ~1023u;
+
+  if (threadIdx.x == 0) {
+    for (int p = 0; p < kSubs; ++p) {
+      SharedCtl& c = ctl_all[p];
+      for (int s = 0; s < kStages; ++s) {
+        ptx::mbar_init(ptx::smem_u32(&c.full[s]), 1);
+        ptx::mbar_init(ptx::smem_u32(&c.empty[s]), 1);
+      }
+      ptx::mbar_init(ptx::smem_u32(&c.acc_full), 1);
+      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[0]), kEpiWarps);
+      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[1]), kEpiWarps);
+      ptx::mbar_init(ptx::smem_u32(&c.drain), 1);
+      c.abort_flag = 0;
+    }
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc<kTmemCols>(ptx::smem_u32(&ctl_all[0].tmem_slot));
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = ctl_all[0].tmem_slot;
+
+  if constexpr (kSubs == 1) {
+    run_pipeline<BN, 0>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+  } else {
+    if (warp < kSubWarps)
+      run_pipeline<BN, 0>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+    else
+      run_pipeline<BN, 1>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
   }
 
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc<kTmemCols>(tmem);
+    ptx::tmem_dealloc<kTmemCols>(tmem_base);
   }
 }
 
@@ -718,6 +760,15 @@ int co_resident_ctas_bn(int* capacity) {
 int co_resident_ctas(int bn, int* capacity) {
   return bn == 64 ? co_resident_ctas_bn<64>(capacity) : co_resident_ctas_bn<128>(capacity);
 }
+// Work-list slots (tile pipelines) of the co-resident grid.
+int tc_subs(int bn) { return bn == 64 ? TcShape<64>::kSubs : TcShape<128>::kSubs; }
+int co_resident_slots(int bn, int* slots) {
+  int ctas = 0;
+  const int rc = co_resident_ctas(bn, &ctas);
+  if (rc) return rc;
+  *slots = ctas * tc_subs(bn);
+  return NMFA_OK;
+}
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -735,8 +786,8 @@ int tc_pick_bn(int32_t replicas) { return replicas <= 64 ? 64 : 128; }
 // ---------------------------------------------------------------------------
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
-  int capacity = 0;
-  int rc = co_resident_ctas(jobs[0].bn, &capacity);
+  int capacity = 0;  // tile pipelines of the co-resident grid
+  int rc = co_resident_slots(jobs[0].bn, &capacity);
   if (rc) return rc;
   size_t ngroups = 0, nitems = 0, flags = 0, state = 0;
   for (int j = 0; j < count; ++j) {
@@ -760,9 +811,13 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
 
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
-  int capacity = 0;
-  int rc = co_resident_ctas(jobs[0].bn, &capacity);
+  int ctas = 0;
+  int rc = co_resident_ctas(jobs[0].bn, &ctas);
   if (rc) return rc;
+  const int subs = tc_subs(jobs[0].bn);
+  // scheduler slot s is pipeline s / ctas of CTA s % ctas: every CTA's first
+  // pipeline fills before any second one
+  const int capacity = ctas * subs;
   int64_t need = 0;
   if ((rc = tc_plan_bytes(jobs, count, &need))) return rc;
   if (need > ws_bytes) return set_error(NMFA_EINVAL, "tensor path: workspace too small");
@@ -834,7 +889,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return gl[x].dur > gl[y].dur; });
   std::vector<double> free_at(capacity, 0.0);
-  std::vector<std::vector<TcItem>> per_cta(capacity);
+  std::vector<std::vector<TcItem>> per_slot(capacity);
   std::vector<int> slots(capacity);
   for (int gi : order) {
     for (int s = 0; s < capacity; ++s) slots[s] = s;
@@ -843,21 +898,23 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     double start = 0.0;
     for (int b = 0; b < nb; ++b) start = std::max(start, free_at[slots[b]]);
     for (int b = 0; b < nb; ++b) {
-      per_cta[slots[b]].push_back(TcItem{gi, b});
+      per_slot[slots[b]].push_back(TcItem{gi, b});
       free_at[slots[b]] = start + gl[gi].dur;
     }
   }
-  int grid = 0;
+  int grid = 0;  // CTAs launched
   for (int s = 0; s < capacity; ++s)
-    if (!per_cta[s].empty()) grid = s + 1;
+    if (!per_slot[s].empty()) grid = std::max(grid, s % ctas + 1);
+  // the kernel's work lists in its order: pipeline-major, sub * grid + cta
   TcItem* hi = reinterpret_cast<TcItem*>(plan->host.data() + off_items);
   int32_t* hf = reinterpret_cast<int32_t*>(plan->host.data() + off_first);
   int32_t pos = 0;
-  for (int s = 0; s < grid; ++s) {
-    hf[s] = pos;
-    for (const TcItem& it : per_cta[s]) hi[pos++] = it;
-  }
-  hf[grid] = pos;
+  for (int p = 0; p < subs; ++p)
+    for (int c = 0; c < grid; ++c) {
+      hf[p * grid + c] = pos;
+      for (const TcItem& it : per_slot[p * ctas + c]) hi[pos++] = it;
+    }
+  hf[subs * grid] = pos;
   plan->dev = base;
   plan->groups_off = 0;
   plan->items_off = off_items;
