@@ -580,7 +580,8 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcGroup* g = groups + items[w].group;
       const int KB = g->n_pad / kKSlot, steps = g->t_f + g->energy_pass;
-      const uint32_t idesc = ptx::idesc_bf16_f32(kBM, static_cast<uint32_t>(g->bn));
+      // every group of a plan has the kernel's tile width: N = BN
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(kBM, BN);
       for (int t = 0; t < steps && ok; ++t, ++gstep) {
         // the epilogue has written this step's bias (h + sigma z d) into the
         // accumulator the step uses; the product accumulates onto it

@@ -265,6 +265,8 @@ def test_full_c2_run_readout_and_energy():
     np.testing.assert_array_equal(out["signs"], np.where(out["state"] >= 0, 1, -1))
     for r in (0, 511, 1023):
         assert out["energy_i64"][r] == oracle.energy_i64(J, out["signs"][r])
+    # Table I: NMFA's mean cut on the N = 2000 SK instance K2000 is an energy density
+    # H / N^1.5 of about -0.73; the reconstructed schedule must land within 5 % of it
     dens = out["energy_i64"].mean() / n ** 1.5
-    assert -0.80 < dens < -0.60, dens
+    assert -0.73 * 1.05 < dens < -0.73 * 0.95, dens
     g.close()
