@@ -64,7 +64,23 @@ __device__ __forceinline__ void draw(NoiseKey key, uint32_t stream, int r0, int 
   for (int g = 0; g < G; ++g) {
     const uint4 w = noise_words(key, stream, static_cast<uint32_t>((r0 >> 2) + g),
                                 static_cast<uint32_t>(t), static_cast<uint32_t>(i));
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && RC < 4) {
+      // fewer than four replicas per thread: only the Box-Muller pair(s) of the
+      // words this thread's replicas use (replica 4p + c takes word c; pair c / 2)
+      const int off = r0 & 3;
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        const int c = off + k;
+        if (k == 0 || (c & 1) == 0) {  // a pair not yet drawn
+          const uint32_t wa = (c & 2) ? w.z : w.x, wb = (c & 2) ? w.w : w.y;
+          const float ra = sqrtf(-2.0f * logf(u01_f32(wa)));
+          float sb, cb;
+          sincospif(2.0f * u01_f32(wb), &sb, &cb);
+          z[k] = (c & 1) ? ra * sb : ra * cb;
+          if (k + 1 < RC && (c & 1) == 0) z[k + 1] = ra * sb;
+        }
+      }
+    } else if constexpr (sizeof(T) == 4) {
       const float4 q = gauss4_f32(w);
       const float qq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -190,8 +206,12 @@ dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
 }
 
 // CSR: coupling sums run over the stored entries of row i in stored order.
+// CSR rows are short (degree 3 for the sparse MAX-CUT classes), so a thread's work per
+// spin is mostly the noise draw and tanh; twice the threads of the dense kernel give
+// the SM more warps to hide their latency.
+constexpr int kCsrThreads = 512;
 template <typename T, int RC, typename VT>
-__global__ void __launch_bounds__(kSimtThreads)
+__global__ void __launch_bounds__(kCsrThreads)
 csr_kernel(CsrProblem pb, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = pb.n;
@@ -390,11 +410,11 @@ int launch_csr_rc(const CsrProblem& pb, const RunParams& rp, cudaStream_t st) {
   if (pb.val_int8) {
     auto k = csr_kernel<T, RC, int8_t>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
-    k<<<grid, kSimtThreads, state_bytes, st>>>(pb, rp);
+    k<<<grid, kCsrThreads, state_bytes, st>>>(pb, rp);
   } else {
     auto k = csr_kernel<T, RC, T>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
-    k<<<grid, kSimtThreads, state_bytes, st>>>(pb, rp);
+    k<<<grid, kCsrThreads, state_bytes, st>>>(pb, rp);
   }
   count_launch();
   return cuda_error(cudaGetLastError(), "CSR kernel launch");
