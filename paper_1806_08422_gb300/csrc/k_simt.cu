@@ -100,6 +100,24 @@ __device__ __forceinline__ void draw(NoiseKey key, uint32_t stream, int r0, int 
   }
 }
 
+// T_t and 1/T_t of step t.  Every thread loads T_t (one address for the whole
+// CTA).  The FP32 path takes the binary32 reciprocal of T_t rounded to binary32:
+// a binary64 division per thread per step was a large share of the FP32 kernels'
+// time on this GPU's narrow FP64 pipe, and a division by one lane shared through a
+// shuffle put its latency in front of every step.  The FP64 path divides by T_t
+// itself and does not use the reciprocal.
+template <typename T>
+__device__ __forceinline__ void step_temperature(const double* Tarr, int t, T& Tt, T& inv_Tt) {
+  const double Td = Tarr[t];
+  if constexpr (sizeof(T) == 4) {
+    Tt = static_cast<float>(Td);
+    inv_Tt = 1.0f / Tt;
+  } else {
+    Tt = Td;
+    inv_Tt = 0.0;
+  }
+}
+
 // The per-spin tail of a step shared by the dense and CSR kernels: normalise,
 // add noise, Boltzmann update (line 7) and alpha-mixing (line 10).
 template <typename T, int RC>
@@ -178,9 +196,8 @@ dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
   T* cur = S0;
   T* nxt = S1;
   for (int t = 0; t < rp.t_f; ++t) {
-    const double Td = rp.T[t];
-    const T Tt = static_cast<T>(Td);
-    const T inv_Tt = static_cast<T>(1.0 / Td);
+    T Tt, inv_Tt;
+    step_temperature<T>(rp.T, t, Tt, inv_Tt);
     double* phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       T acc[RC];
@@ -229,9 +246,8 @@ csr_kernel(CsrProblem pb, RunParams rp) {
   T* cur = S0;
   T* nxt = S1;
   for (int t = 0; t < rp.t_f; ++t) {
-    const double Td = rp.T[t];
-    const T Tt = static_cast<T>(Td);
-    const T inv_Tt = static_cast<T>(1.0 / Td);
+    T Tt, inv_Tt;
+    step_temperature<T>(rp.T, t, Tt, inv_Tt);
     double* phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       T acc[RC];
@@ -435,6 +451,25 @@ int pick_rc(int n, int replicas, size_t elem, int requested) {
   return rc;
 }
 
+// Replica block of the CSR kernel.  A thread works through ceil(n / kCsrThreads)
+// spins per step, and each Philox call serves four replicas, so wide blocks pay off
+// once the rows fill much of the CTA; small n wants more CTAs (measured on GB300,
+// FP32, 512 replicas, ms per 1000-step run: n = 100: 0.94 / 0.76 / 0.99 for 1 / 2 / 4
+// replicas per CTA; n = 400: 2.48 / 1.44 / 1.30; n = 2000: 9.58 / 5.19 / 4.68).  The
+// grid may then fall a little short of the SM count (down to 80 %).
+int pick_rc_csr(int n, int replicas, size_t elem, int requested) {
+  if (requested > 0) return requested;
+  int sms = 148;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t limit = static_cast<size_t>(max_smem_optin());
+  int rc = n < kCsrThreads / 2 ? 2 : 4;
+  while (rc > 1 && 2ull * n * rc * elem > limit) rc >>= 1;
+  while (rc > 1 && 5 * ((replicas + rc - 1) / rc) < 4 * sms) rc >>= 1;
+  return rc;
+}
+
 }  // namespace
 
 int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
@@ -502,7 +537,8 @@ int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, floa
 
 int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,
                int replicas_per_cta) {
-  const int rc = pick_rc(pb.n, rp.replicas, fp64 ? 8 : 4, replicas_per_cta);
+  const int rc = fp64 ? pick_rc(pb.n, rp.replicas, 8, replicas_per_cta)
+                      : pick_rc_csr(pb.n, rp.replicas, 4, replicas_per_cta);
   if (fp64) {
     switch (rc) {
       case 1: return launch_csr_rc<double, 1>(pb, rp, st);

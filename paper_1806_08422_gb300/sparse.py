@@ -35,6 +35,7 @@ def main():
     ap.add_argument("--t-f", type=int, default=1000)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--rc", type=int, default=0, help="replicas per CTA (0: the library's pick)")
     args = ap.parse_args()
 
     import torch
@@ -45,6 +46,8 @@ def main():
     for kind, n, J in instances():
         row_ptr, col, val = inst.to_csr(J)
         p = nmfa.Problem(csr=(row_ptr, col, val), n=n, precision=args.precision)
+        if args.rc:
+            nmfa.nmfa_tune_replicas_per_cta(p.handle, args.rc)
         signs = torch.empty((R, n), dtype=torch.int8, device=dev)
         e = torch.empty(R, dtype=torch.int64, device=dev)
         stream = torch.cuda.current_stream()
@@ -64,7 +67,7 @@ def main():
         per = float(np.median(ms)) / 1e3
         units = n * R * args.t_f
         print(json.dumps({"instance": kind, "n": n, "nnz": int(len(col)), "replicas": R, "t_f": args.t_f,
-                          "precision": args.precision, "ms_per_run": float(np.median(ms)),
+                          "precision": args.precision, "rc": args.rc, "ms_per_run": float(np.median(ms)),
                           "kernel_ms": float(np.median(kms)), "spin_updates_per_s": units / per,
                           "min_energy": int(e.min().item())}), flush=True)
         p.close()
