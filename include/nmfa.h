@@ -63,7 +63,7 @@ typedef struct nmfa_problem nmfa_problem; /* opaque; owns device copies of (h, J
 
 /*
  * nmfa_create -- upload a dense Ising problem (Eq. (1)) and precompute, on the GPU in
- * FP64, the row norms d_i = sqrt(h_i^2 + sum_j J_ij^2) of Algorithm 1 line 6
+ * FP64, the row norms d_i = sqrt(h_i^2 + sum_j J_ij^2) of Algorithm 1's field
  * (Sec. II: the root mean square of the terms acting on spin i).  A spin with
  * d_i = 0 gets a normalised field of 0.
  *   n         number of spins, 1 <= n <= 65536 (the CUDA-core paths accept less;
@@ -103,7 +103,7 @@ void nmfa_destroy(nmfa_problem* p);
  *                  schedule is an input; see the instance module for a default)
  *   t_f            number of steps, >= 0 (0 reads out the initial zero state)
  *   sigma          standard deviation of the Gaussian noise, >= 0 (Sec. II)
- *   alpha          mixing constant, 0 < alpha <= 1 (Algorithm 1 line 10)
+ *   alpha          mixing constant, 0 < alpha <= 1 (Algorithm 1's alpha-mix)
  *   replicas       R >= 1
  *   seed,stream_id select the noise stream (see the conventions above)
  *   signs_out      host, R*n int8 (may be NULL)

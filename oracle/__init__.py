@@ -10,7 +10,7 @@ this module only compiles it with gcc and marshals numpy arrays through ctypes.
 Function map (paper passages in the C file's comments):
   philox4x32_10  -- counter-based generator of Salmon et al. (SC'11)
   gauss          -- the N(0,1) draw for (replica, step, spin); Box-Muller
-  row_norms      -- d_i of Algorithm 1 line 6 (Sec. II)
+  row_norms      -- d_i of Algorithm 1's field update (Sec. II)
   run_dense/run_csr -- Algorithm 1, with readout and Eq. (1) energies
   energy/energy_i64 -- Eq. (1), unordered pairs counted once
   brute_force    -- exhaustive ground state for small n

@@ -88,7 +88,7 @@ ORC_EXPORT double orc_gauss(uint64_t seed, uint32_t stream, int64_t r, int32_t t
 }
 
 /* ------------------------------------------------------------------------- */
-/* Row normalisation of Algorithm 1, line 6: d_i = sqrt(h_i^2 + sum_j J_ij^2),  */
+/* Row normalisation of Algorithm 1's field: d_i = sqrt(h_i^2 + sum_j J_ij^2),  */
 /* the root mean square of the Hamiltonian terms acting on spin i (Sec. II).    */
 /* Sum over j ascending, then add h_i^2.                                        */
 /* ------------------------------------------------------------------------- */

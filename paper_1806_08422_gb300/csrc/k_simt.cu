@@ -4,7 +4,7 @@
 // Dense and CSR annealing use the same "replica-resident" design: one CTA owns a
 // block of `RC` replicas for ALL n spins, keeps their state s in shared memory
 // (two buffers: Algorithm 1 computes every Phi_i from the old state before any
-// s_i changes, lines 5-11), runs all t_f steps in one launch, and reads out the
+// s_i changes, as Algorithm 1's two loops per step require), runs all t_f steps in one launch, and reads out the
 // signs at the end.  No CTA waits on another, so the launch needs no grid barrier.
 // Thread i computes Phi_i for the CTA's replicas; for symmetric J, row i equals
 // column i, so J[j*n + i] for fixed j is read coalesced across the warp.
@@ -119,7 +119,7 @@ __device__ __forceinline__ void step_temperature(const double* Tarr, int t, T& T
 }
 
 // The per-spin tail of a step shared by the dense and CSR kernels: normalise,
-// add noise, Boltzmann update (line 7) and alpha-mixing (line 10).
+// add noise, Boltzmann update and alpha-mixing of Algorithm 1.
 template <typename T, int RC>
 __device__ __forceinline__ void finish_spin(const T acc[RC], int i, int t, int r0, int R,
                                             int n, T hi, double di, float inv_di, T sigma,
@@ -373,7 +373,7 @@ __global__ void tiled_f32_init_kernel(int n, int R, int ld, const double* s0, fl
   }
 }
 
-// Readout (Algorithm 1 lines 13-15) of the [n][ld] state into replica-major signs.
+// Sign readout (Algorithm 1) of the [n][ld] state into replica-major signs.
 __global__ void tiled_f32_readout_kernel(int n, int R, int ld, const float* S, int8_t* signs, double* s_out) {
   const int64_t total = static_cast<int64_t>(n) * R;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
@@ -712,7 +712,7 @@ int launch_energy(const EnergyProblem& ep, const int8_t* signs, int32_t replicas
 }
 
 // ----------------------------------------------------------------------------
-// Preparation (Algorithm 1 line 6 denominators, computed once per problem in
+// Preparation (the denominators of Algorithm 1's field update, computed once per problem in
 // FP64): d_i = sqrt(h_i^2 + sum_j J_ij^2), sum over j ascending, unfused.
 // ----------------------------------------------------------------------------
 __global__ void row_norms_dense_kernel(int n, const double* __restrict__ J64,

@@ -1,33 +1,39 @@
 // k_tc.cu -- the tcgen05 tensor-core path of NMFA (BF16 J and S, FP32 accumulation).
 //
-// One persistent launch runs all t_f steps of Algorithm 1 for a batch of replicas.
-// The coupling product of line 6 over all replicas is the GEMM P = J S (J: n x n,
-// S: n x R); CTA (b, c) owns the output tile of spins [128 b, 128 b + 128) and
-// replicas [BN c, BN c + BN) for the whole run:
-//   - warp 0 streams 128-deep K slices of J's row block and of S's replica block
-//     into a 3-slot shared-memory ring with TMA (128-byte swizzle); the J
-//     slices of a step start before the step's state is published, the S slices
-//     after the whole warp has seen every row block's epoch flag of the replica
-//     block reach the step;
-//   - warp 1 issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of the
-//     converged warp) into a TMEM accumulator, releasing ring slots and the
-//     accumulator with tcgen05.commit;
-//   - warps 2..17 first draw the step's noise (Philox/Box-Muller, independent of
-//     the state) while the tensor core works and park sigma*z in TMEM; once the
-//     accumulator is complete they read it with tcgen05.ld and finish the step:
-//     normalisation by d_i, -tanh(Phi/T_t) and the alpha-mix into the FP32 master
-//     state, which stays in TMEM for the whole run (line 10); the new state is
-//     written in BF16 to the next of two global S buffers (L2-resident) and
-//     published by each warp's release increment of the tile's epoch counter.
-// Step t+1's slices of row block b' are loaded only after tile (b', c) has
-// published step t, which realises the synchronous update of Algorithm 1
-// (every Phi from the old state) without a grid-wide barrier: only the CTAs of
-// one replica block depend on one another.  After the last step the signs are
-// read out from the FP32 master state (lines 13-15).
+// One persistent launch runs all t_f steps of Algorithm 1 for a batch of replicas
+// (one run, or a ragged batch of runs of different instances).  The coupling
+// product of the field update over all replicas is the GEMM P = J S (J: n x n,
+// S: n x R).  The replicas of a run are split into groups of BN (64 or 128); a
+// group's output is tiled by row blocks of 128 spins, and each (group, row block)
+// item is owned by one tile pipeline for the group's whole run.  A pipeline is a
+// TMA warp, an MMA warp and BN / 8 epilogue warps; a CTA holds one pipeline for
+// BN = 128 and two independent ones for BN = 64 (one CTA per SM), and walks the
+// work list the host planned for it:
+//   - the TMA warp streams 128-deep K slices of J's row block and of S's replica
+//     block into a ring of shared-memory slots (128-byte swizzle); the J slices of
+//     a step start before the step's state is published, the S slices after the
+//     whole warp has seen every row block's epoch flag of the group reach the step;
+//   - the MMA warp issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of
+//     the converged warp) into one of two TMEM accumulators, releasing ring slots
+//     and the accumulator with tcgen05.commit;
+//   - the epilogue warps draw the next step's noise (Philox/Box-Muller, independent
+//     of the state) while the tensor core works and write h_i + sigma z d_i into
+//     the next accumulator, so that the product lands on it; once the accumulator
+//     is complete they read it with tcgen05.ld and finish the step: division by
+//     d_i, -tanh(Phi/T_t) and the alpha-mix into the FP32 master state, which stays
+//     in TMEM for the whole run; the new state is written in BF16 to the next of
+//     two global S buffers (L2-resident) and published by each warp's release
+//     increment of the tile's epoch counter.
+// Step t+1's slices of row block b' are loaded only after tile b' has published
+// step t, which realises the synchronous update of Algorithm 1 (every Phi from the
+// old state) without a grid-wide barrier: only the pipelines of one group depend on
+// one another.  After the last step the signs are read out from the FP32 master
+// state; for integer problems one more product of J with the sign vectors gives the
+// Eq. (1) energies exactly.
 //
 // Every wait (mbarrier or flag) is bounded by a 2-second wall-clock limit; on
-// expiry the CTA records NMFA's timeout status, drains its own TMA copies and
-// MMAs, frees its TMEM and returns.
+// expiry the pipeline records NMFA's timeout status, drains its own TMA copies and
+// MMAs, and the CTA frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -57,7 +63,7 @@ constexpr int kColsPerWarp = 32;
 // [A atom 0][A atom 1][B atom 0][B atom 1].
 constexpr int kAtoms = 2;
 constexpr int kKSlot = kAtoms * kBK;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 3;
 constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 // Geometry per tile width BN (replicas per tile, the MMA's N: 64 or 128).
 //   Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
@@ -91,12 +97,12 @@ struct TcShape {
 };
 constexpr int kMaxSubs = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-// A CTA that reaches a new group early waits for the group's other CTAs to finish
-// the groups scheduled before it; that first wait gets a longer bound.
+// A pipeline that reaches a new group early waits for the group's other pipelines to
+// finish the groups scheduled before it; that first wait gets a longer bound.
 constexpr uint64_t kStartTimeoutNs = 20000000000ull;
 constexpr uint64_t kDrainNs = 200000000ull;
 
-// One replica block of one instance: the CTAs that exchange state every step.
+// One replica block of one instance: the tile pipelines that exchange state every step.
 struct __align__(64) TcGroup {
   CUtensorMap tmJ;        // BF16 J of the instance, [n_pad][n_pad], box 64 x 128
   CUtensorMap tmS;        // this group's state buffers, [2 * bn][n_pad], box 64 x bn
@@ -321,7 +327,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   uint32_t* my_flag = g->flags + b;
   uint32_t v[16], m[16];
 
-  // initial state (line 2, or the given s0) -> master in TMEM and BF16 buffer 0
+  // the initial state (zero, or the given s0) -> master in TMEM and BF16 buffer 0
   const double* s0 = g->s0;
 #pragma unroll 1
   for (int cc = 0; cc < kCW; cc += 16) {
@@ -411,7 +417,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     __syncwarp();
     if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
   }
-  // readout (lines 13-15): sign of the FP32 master state, zero reads as +1
+  // sign readout of Algorithm 1: sign of the FP32 master state, zero reads as +1
   if (!__all_sync(0xffffffffu, !aborted(ctl))) return false;
   int8_t* signs = g->signs;
   double* s_out = g->s_out;

@@ -1,6 +1,6 @@
 // nmfa_device.cuh -- device helpers shared by the NMFA kernels: the Philox4x32-10
 // counter-based generator (Salmon et al., SC'11), the uniform mapping and the
-// Box-Muller transform that turn it into the N(0, 1) draws of Algorithm 1 line 6.
+// Box-Muller transform that turn it into the N(0, 1) draws of Algorithm 1's field update.
 //
 // Stream layout (fixed for every kernel of the library):
 //   counter = (r / 4, t, i, stream_id), key = (seed low 32 bits, seed high 32 bits)

@@ -1,6 +1,6 @@
 """Parity of the CUDA paths (through the C ABI) with the FP64 oracle.
 
-Tolerances (Algorithm 1 line 6, from identical state; "relative" is measured
+Tolerances (Algorithm 1's field Phi, from identical state; "relative" is measured
 against the forward-error scale (|h_i| + sum_j |J_ij s_j|)/d_i + sigma |z|):
   FP64 <= 1e-12, FP32 <= 1e-5, BF16 (tensor path) <= 4e-3.
 sigma = 0 FP64 trajectories agree to <= 1e-9 over t_f = 1000 steps; energies of

@@ -29,7 +29,7 @@ def _kat_rows():
 
 
 # --------------------------------------------------------------------------
-# Noise stream (Algorithm 1 line 6: N(0, sigma); Sec. II: sigma is a standard
+# Noise stream (Algorithm 1's field: N(0, sigma); Sec. II: sigma is a standard
 # deviation).  Philox4x32-10 from its published known-answer vectors.
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("row", _kat_rows())
@@ -64,7 +64,7 @@ def test_gauss_streams_differ():
 
 
 # --------------------------------------------------------------------------
-# Row norms (Algorithm 1 line 6; Sec. II: the root mean square of the terms
+# Row norms (Algorithm 1's field; Sec. II: the root mean square of the terms
 # acting on a spin).  Closed forms for the paper's instance classes.
 # --------------------------------------------------------------------------
 def test_row_norms_closed_forms():
@@ -79,7 +79,7 @@ def test_row_norms_closed_forms():
 
 # --------------------------------------------------------------------------
 # Step 1 of Algorithm 1 from s = 0:  s_1 = -alpha tanh((h_i/d_i + sigma z)/T_1)
-# (lines 1-11).  With sigma = 0 this is a closed form; with sigma > 0 the
+# (Algorithm 1).  With sigma = 0 this is a closed form; with sigma > 0 the
 # recovered z must be the stream's draw for (r, t=0, i) and standard normal.
 # --------------------------------------------------------------------------
 def test_step1_closed_form_sigma0():
@@ -113,7 +113,7 @@ def test_step1_recovers_noise_stream():
 
 # --------------------------------------------------------------------------
 # Invariants of Algorithm 1: |s_i(t)| <= 1 - (1 - alpha)^t from s = 0, since
-# |tanh| < 1 and each step is a convex combination (lines 9-11).
+# |tanh| < 1 and each step is a convex combination (Algorithm 1's alpha-mix).
 # --------------------------------------------------------------------------
 def test_state_bound():
     n, alpha = 30, 0.15
@@ -203,7 +203,7 @@ def test_zero_temperature_sign_dynamics():
 
 
 def test_coupling_product_against_compensated_sum():
-    # Algorithm 1 line 6 with sigma = 0 from a given state: Phi = (h + J s)/d.
+    # Algorithm 1's field with sigma = 0 from a given state: Phi = (h + J s)/d.
     n, R = 70, 3
     J = inst.random_real_couplings(n, 20, density=0.6)
     h = inst.random_fields(n, 0.3, 21)
