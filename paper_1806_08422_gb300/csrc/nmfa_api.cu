@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "nmfa_internal.h"
@@ -150,6 +151,175 @@ bool e4m3_exact(double v) {
   return mant8 == std::floor(mant8);
 }
 
+// Host-side scan of a dense problem at creation: finiteness, zero diagonal,
+// symmetry, integrality, the int8/BF16/E4M3 storage checks and the largest
+// sum_j |J_ij| + 2 |h_i|.  Rows go in blocks of 32 to up to 16 threads; the symmetry
+// check compares 32 x 32 tiles with their transposes, so that both reads stay in
+// cache.  Errors are reported by kind in a fixed order (non-finite, diagonal,
+// symmetry), not by position.
+struct DenseScan {
+  bool finite = true, diag_zero = true, symmetric = true;
+  bool integer = true, int8_ok = true, bf16_ok = true, e4m3_ok = true;
+  double max_row = 0.0;
+};
+
+void scan_rows(int32_t n, const double* h, const double* J, bool want_bf16, bool want_e4m3, int first_block,
+               int stride, DenseScan* out) {
+  constexpr int kB = 32;
+  DenseScan r;
+  const int64_t ln = n;
+  for (int32_t ib = first_block * kB; ib < n; ib += stride * kB) {
+    const int32_t ie = std::min(n, ib + kB);
+    for (int32_t i = ib; i < ie; ++i) {
+      double row = 0.0;
+      if (h != nullptr) {
+        const double hv = h[i];
+        if (!std::isfinite(hv)) r.finite = false;
+        if (hv != std::nearbyint(hv) || std::fabs(hv) >= 2147483648.0) r.integer = false;
+        row = 2.0 * std::fabs(hv);
+      }
+      if (J[i * ln + i] != 0.0) r.diag_zero = false;
+      const double* Ji = J + i * ln;
+      for (int32_t j = 0; j < n; ++j) {
+        const double v = Ji[j];
+        const double a = std::fabs(v);
+        if (!std::isfinite(v)) r.finite = false;
+        if (v != std::nearbyint(v) || a >= 2147483648.0) r.integer = false;
+        if (a > 127.0) r.int8_ok = false;
+        row += a;
+        // integers up to 16 in magnitude are exact in both BF16 and E4M3
+        if (!(a <= 16.0 && v == std::nearbyint(v))) {
+          if (want_bf16 && r.bf16_ok && !bf16_exact(v)) r.bf16_ok = false;
+          if (want_e4m3 && r.e4m3_ok && !e4m3_exact(v)) r.e4m3_ok = false;
+        }
+      }
+      r.max_row = std::max(r.max_row, row);
+    }
+    // symmetry: tiles (ib, jb) with jb >= ib against their transposes
+    for (int32_t jb = ib; jb < n && r.symmetric; jb += kB) {
+      const int32_t je = std::min(n, jb + kB);
+      for (int32_t i = ib; i < ie; ++i)
+        for (int32_t j = std::max(jb, i + 1); j < je; ++j)
+          if (J[i * ln + j] != J[j * ln + i]) r.symmetric = false;
+    }
+  }
+  *out = r;
+}
+
+DenseScan scan_dense(int32_t n, const double* h, const double* J, int32_t precision) {
+  const bool want_bf16 = precision == NMFA_BF16, want_e4m3 = precision == NMFA_BF16_FP8J;
+  int threads = 1;
+  if (n >= 1024) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    threads = static_cast<int>(std::min<unsigned>(16u, hc == 0 ? 1u : hc));
+  }
+  std::vector<DenseScan> parts(threads);
+  if (threads == 1) {
+    scan_rows(n, h, J, want_bf16, want_e4m3, 0, 1, &parts[0]);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; ++t) pool.emplace_back(scan_rows, n, h, J, want_bf16, want_e4m3, t, threads, &parts[t]);
+    for (auto& th : pool) th.join();
+  }
+  DenseScan r;
+  for (const DenseScan& q : parts) {
+    r.finite = r.finite && q.finite;
+    r.diag_zero = r.diag_zero && q.diag_zero;
+    r.symmetric = r.symmetric && q.symmetric;
+    r.integer = r.integer && q.integer;
+    r.int8_ok = r.int8_ok && q.int8_ok;
+    r.bf16_ok = r.bf16_ok && q.bf16_ok;
+    r.e4m3_ok = r.e4m3_ok && q.e4m3_ok;
+    r.max_row = std::max(r.max_row, q.max_row);
+  }
+  return r;
+}
+
+// Host-built device copies of a tensor-path problem with integer |J_ij| <= 127 and
+// integer |h_i| <= 2^20: every term of d_i^2 = h_i^2 + sum_j J_ij^2 is an integer
+// and the sum stays below 2^53, so d_i computed here is bit-identical to the device
+// kernel's (exact sum, correctly rounded square root), and the BF16 / E4M3 / int8
+// copies are exact conversions.  Building them on the host avoids a binary64 device
+// copy of J (8 n^2 bytes) and the device-wide synchronisation of freeing it, which
+// otherwise stalls problem creation behind running kernels.
+struct HostCompact {
+  std::vector<double> d64;       // n
+  std::vector<float> inv_d32;    // n_pad, 0 where d_i = 0 and in the padding
+  std::vector<float> h32;        // n_pad, 0 in the padding
+  std::vector<uint8_t> Jq;       // n_pad x n_pad BF16 or E4M3, zero-padded
+  std::vector<int8_t> J8;        // n x ld8, rows padded with zeros
+  int64_t ld8 = 0;
+};
+
+uint8_t e4m3_bits(double v) {  // v exactly representable, |v| <= 448
+  const uint8_t sign = std::signbit(v) ? 0x80 : 0x00;
+  const double a = std::fabs(v);
+  if (a == 0.0) return sign;
+  int e = 0;
+  const double fr = std::frexp(a, &e);  // a = (2 fr) * 2^(e - 1)
+  const int ex = e - 1;
+  if (ex < -6) return static_cast<uint8_t>(sign | static_cast<int>(std::ldexp(a, 9)));  // subnormal: k * 2^-9
+  const int mant = static_cast<int>((2.0 * fr - 1.0) * 8.0);
+  return static_cast<uint8_t>(sign | ((ex + 7) << 3) | mant);
+}
+
+uint16_t bf16_bits(double v) {  // v exactly representable in BF16
+  const float f = static_cast<float>(v);
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return static_cast<uint16_t>(b >> 16);
+}
+
+void compact_rows(int32_t n, int32_t n_pad, const double* h, const double* J, bool fp8, int first_block, int stride,
+                  HostCompact* hc) {
+  constexpr int kB = 32;
+  const int64_t ln = n, lp = n_pad;
+  for (int32_t ib = first_block * kB; ib < n; ib += stride * kB) {
+    const int32_t ie = std::min(n, ib + kB);
+    for (int32_t i = ib; i < ie; ++i) {
+      const double* Ji = J + i * ln;
+      double sq = 0.0;
+      for (int32_t j = 0; j < n; ++j) {
+        const double v = Ji[j];
+        sq += v * v;
+        hc->J8[i * hc->ld8 + j] = static_cast<int8_t>(v);
+        if (fp8) {
+          hc->Jq[i * lp + j] = e4m3_bits(v);
+        } else {
+          const uint16_t b = bf16_bits(v);
+          std::memcpy(&hc->Jq[2 * (i * lp + j)], &b, 2);
+        }
+      }
+      const double hv = h != nullptr ? h[i] : 0.0;
+      const double d = std::sqrt(hv * hv + sq);
+      hc->d64[i] = d;
+      hc->inv_d32[i] = d > 0.0 ? static_cast<float>(1.0 / d) : 0.0f;
+      hc->h32[i] = static_cast<float>(hv);
+    }
+  }
+}
+
+void build_compact(int32_t n, int32_t n_pad, const double* h, const double* J, bool fp8, HostCompact* hc) {
+  hc->ld8 = (n + 15) / 16 * 16;
+  hc->d64.assign(n, 0.0);
+  hc->inv_d32.assign(std::max(n, n_pad), 0.0f);
+  hc->h32.assign(std::max(n, n_pad), 0.0f);
+  hc->Jq.assign(static_cast<size_t>(n_pad) * n_pad * (fp8 ? 1 : 2), 0);
+  hc->J8.assign(static_cast<size_t>(n) * hc->ld8, 0);
+  int threads = 1;
+  if (n >= 1024) {
+    const unsigned c = std::thread::hardware_concurrency();
+    threads = static_cast<int>(std::min<unsigned>(16u, c == 0 ? 1u : c));
+  }
+  if (threads == 1) {
+    compact_rows(n, n_pad, h, J, fp8, 0, 1, hc);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < threads; ++t) pool.emplace_back(compact_rows, n, n_pad, h, J, fp8, t, threads, hc);
+  for (auto& th : pool) th.join();
+}
+
 int validate_common(int32_t n, int32_t precision) {
   if (n < 1 || n > 65536) return set_error(NMFA_EINVAL, "n must be in [1, 65536]");
   if (precision < NMFA_FP64 || precision > NMFA_BF16_FP8J)
@@ -167,7 +337,7 @@ int check_device() {
   return NMFA_OK;
 }
 
-int finish_create(nmfa_problem* p, const double* h) {
+int finish_create(nmfa_problem* p, const double* h, const HostCompact* hc = nullptr) {
   int rc;
   if ((rc = cuda_error(cudaGetDevice(&p->device), "cudaGetDevice"))) return rc;
   if ((rc = cuda_error(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking), "stream")))
@@ -190,6 +360,20 @@ int finish_create(nmfa_problem* p, const double* h) {
   }
   // h in binary32, zero-padded to n_pad for the tensor path's padded rows
   if ((rc = dev_alloc_t(p, &p->h32, std::max(n, p->n_pad)))) return rc;
+  if (hc != nullptr) {
+    // norms and binary32 copies built on the host (exact for these problems)
+    const size_t np = std::max(n, p->n_pad);
+    if ((rc = cuda_error(cudaMemcpyAsync(p->h32, hc->h32.data(), sizeof(float) * np, cudaMemcpyHostToDevice, st),
+                         "h upload")) ||
+        (rc = cuda_error(cudaMemcpyAsync(p->inv_d32, hc->inv_d32.data(), sizeof(float) * np, cudaMemcpyHostToDevice,
+                                         st),
+                         "norm upload")) ||
+        (rc = cuda_error(cudaMemcpyAsync(p->d64, hc->d64.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st),
+                         "norm upload")))
+      return rc;
+    if ((rc = cuda_error(cudaMemsetAsync(p->status, 0, 4, st), "status clear"))) return rc;
+    return cuda_error(cudaStreamSynchronize(st), "create");
+  }
   if ((rc = cuda_error(cudaMemsetAsync(p->h32, 0, sizeof(float) * std::max(n, p->n_pad), st), "h clear"))) return rc;
   if ((rc = cuda_error(cudaMemsetAsync(p->inv_d32, 0, sizeof(float) * std::max(n, p->n_pad), st), "norm clear")))
     return rc;
@@ -235,37 +419,17 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
   int rc = validate_common(n, precision);
   if (rc) return rc;
   if (J == nullptr) return set_error(NMFA_EINVAL, "J is NULL");
-  bool integer = true, int8_ok = true, bf16_ok = true, e4m3_ok = true;
-  double max_row = 0.0;  // max_i (sum_j |J_ij| + 2 |h_i|)
-  for (int32_t i = 0; i < n; ++i) {
-    double row = 0.0;
-    if (h != nullptr) {
-      if (!std::isfinite(h[i])) return set_error(NMFA_EINVAL, "h has a non-finite entry");
-      if (h[i] != std::nearbyint(h[i]) || std::fabs(h[i]) >= 2147483648.0) integer = false;
-      row = 2.0 * std::fabs(h[i]);
-    }
-    if (J[static_cast<int64_t>(i) * n + i] != 0.0) return set_error(NMFA_EDIAG, "J has a nonzero diagonal entry");
-    for (int32_t j = 0; j < n; ++j) {
-      const double v = J[static_cast<int64_t>(i) * n + j];
-      if (!std::isfinite(v)) return set_error(NMFA_EINVAL, "J has a non-finite entry");
-      if (j > i && v != J[static_cast<int64_t>(j) * n + i]) return set_error(NMFA_ENOTSYM, "J is not symmetric");
-      if (v != std::nearbyint(v) || std::fabs(v) >= 2147483648.0) integer = false;
-      if (std::fabs(v) > 127.0) int8_ok = false;
-      row += std::fabs(v);
-    }
-    max_row = std::max(max_row, row);
-  }
-  int8_ok = int8_ok && integer && static_cast<int64_t>(n) * 127 < (1ll << 30);
-  if (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) {
-    for (int64_t q = 0; q < static_cast<int64_t>(n) * n; ++q) {
-      if (precision == NMFA_BF16 && bf16_ok && !bf16_exact(J[q])) bf16_ok = false;
-      if (precision == NMFA_BF16_FP8J && e4m3_ok && !e4m3_exact(J[q])) e4m3_ok = false;
-    }
-    if (precision == NMFA_BF16 && !bf16_ok)
-      return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in BF16");
-    if (precision == NMFA_BF16_FP8J && !e4m3_ok)
-      return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in FP8 E4M3");
-  }
+  const DenseScan sc = scan_dense(n, h, J, precision);
+  if (!sc.finite) return set_error(NMFA_EINVAL, "h or J has a non-finite entry");
+  if (!sc.diag_zero) return set_error(NMFA_EDIAG, "J has a nonzero diagonal entry");
+  if (!sc.symmetric) return set_error(NMFA_ENOTSYM, "J is not symmetric");
+  const bool integer = sc.integer;
+  const bool int8_ok = sc.int8_ok && integer && static_cast<int64_t>(n) * 127 < (1ll << 30);
+  const double max_row = sc.max_row;
+  if (precision == NMFA_BF16 && !sc.bf16_ok)
+    return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in BF16");
+  if (precision == NMFA_BF16_FP8J && !sc.e4m3_ok)
+    return set_error(NMFA_EUNSUPPORTED, "J is not exactly representable in FP8 E4M3");
   if ((rc = check_device())) return rc;
   nmfa_problem* p = new nmfa_problem();
   p->n = n;
@@ -281,6 +445,28 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
     t_last_error = msg;
     return code;
   };
+  // Tensor-path problems with |J_ij| <= 127 integers and small integer h are
+  // prepared on the host (see HostCompact); the rest go through a binary64 device
+  // copy of J.
+  bool compact = (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) && int8_ok;
+  if (compact && h != nullptr)
+    for (int32_t i = 0; i < n && compact; ++i) compact = std::fabs(h[i]) <= 1048576.0;
+  if (compact) {
+    HostCompact hc;
+    build_compact(n, p->n_pad, h, J, precision == NMFA_BF16_FP8J, &hc);
+    if ((rc = finish_create(p, h, &hc))) return fail(rc);
+    st = p->own_stream;
+    void* q = nullptr;
+    if ((rc = dev_alloc(p, &q, hc.Jq.size()))) return fail(rc);
+    p->Jq = q;
+    if ((rc = dev_alloc_t(p, &p->J8, hc.J8.size()))) return fail(rc);
+    if ((rc = cuda_error(cudaMemcpyAsync(p->Jq, hc.Jq.data(), hc.Jq.size(), cudaMemcpyHostToDevice, st), "J upload")) ||
+        (rc = cuda_error(cudaMemcpyAsync(p->J8, hc.J8.data(), hc.J8.size(), cudaMemcpyHostToDevice, st), "J upload")) ||
+        (rc = cuda_error(cudaStreamSynchronize(st), "J upload")))
+      return fail(rc);
+    *out = p;
+    return NMFA_OK;
+  }
   if ((rc = dev_alloc_t(p, &p->J64, static_cast<size_t>(n) * n))) return fail(rc);
   if ((rc = cuda_error(cudaMemcpy(p->J64, J, sizeof(double) * n * static_cast<size_t>(n), cudaMemcpyHostToDevice), "J upload")))
     return fail(rc);
