@@ -204,11 +204,12 @@ typedef struct nmfa_batch nmfa_batch;
 #define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128) per job by timing */
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
 
-/* Plans the batch (tiles of 128 spins x 64 or 128 replicas; the CTAs of one replica
- * block are co-scheduled on the persistent grid by list scheduling), allocates its
- * workspace, uploads the plan and, with NMFA_BATCH_GRAPH, captures the launch
- * sequence as a CUDA graph.  The problems and every device buffer named in `jobs`
- * must stay valid while the batch exists; each launch overwrites the outputs. */
+/* Plans the batch (tiles of 128 spins x 64 or 128 replicas; the tile pipelines of
+ * one replica block are co-scheduled on the persistent grid by list scheduling),
+ * allocates its workspace, uploads the plan and, with NMFA_BATCH_GRAPH, captures the
+ * launch sequence as a CUDA graph.  Nothing runs until nmfa_batch_launch.  The
+ * problems and every device buffer named in `jobs` must stay valid while the batch
+ * exists; each launch overwrites the outputs. */
 int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32_t count,
                       int32_t options, nmfa_batch** out);
 /* Enqueues one execution of the whole batch on `cuda_stream` (ordered after the

@@ -935,22 +935,29 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   return NMFA_OK;
 }
 
-// Enqueue: upload the plan (from kernel parameters), clear the epoch counters,
-// launch the persistent kernel.  Everything is stream-ordered and capturable.
+// Upload the plan (group descriptors, items, per-pipeline offsets) from kernel
+// parameters: no host-pinned buffer and no allocation, so it can be recorded in a
+// CUDA graph.  Stream-ordered.
+int tc_upload_plan(const TcPlan& plan, cudaStream_t st) {
+  const size_t total = plan.flags_off;  // descriptors, items and offsets precede the flags
+  TcUpload u;
+  for (size_t off = 0; off < total; off += kUploadBytes) {
+    const size_t chunk = std::min<size_t>(kUploadBytes, total - off);
+    u.bytes = static_cast<uint32_t>(chunk);
+    std::memcpy(u.data, plan.host.data() + off, chunk);
+    tc_upload_kernel<<<1, 256, 0, st>>>(u, reinterpret_cast<uint4*>(static_cast<char*>(plan.dev) + off));
+    count_launch();
+    const int rc = cuda_error(cudaGetLastError(), "plan upload");
+    if (rc) return rc;
+  }
+  return NMFA_OK;
+}
+
+// Enqueue: upload the plan if asked, clear the epoch counters, launch the
+// persistent kernel.  Everything is stream-ordered and capturable.
 int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   int rc;
-  if (upload) {
-    const size_t total = plan.flags_off;  // descriptors, items and offsets precede the flags
-    TcUpload u;
-    for (size_t off = 0; off < total; off += kUploadBytes) {
-      const size_t chunk = std::min<size_t>(kUploadBytes, total - off);
-      u.bytes = static_cast<uint32_t>(chunk);
-      std::memcpy(u.data, plan.host.data() + off, chunk);
-      tc_upload_kernel<<<1, 256, 0, st>>>(u, reinterpret_cast<uint4*>(static_cast<char*>(plan.dev) + off));
-      count_launch();
-      if ((rc = cuda_error(cudaGetLastError(), "plan upload"))) return rc;
-    }
-  }
+  if (upload && (rc = tc_upload_plan(plan, st))) return rc;
   if ((rc = cuda_error(cudaMemsetAsync(static_cast<char*>(plan.dev) + plan.flags_off, 0, plan.flags_bytes, st),
                        "flag reset")))
     return rc;

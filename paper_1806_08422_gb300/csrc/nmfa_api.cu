@@ -1029,9 +1029,9 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
                             &b->plans.back())))
       return fail(rc);
     // upload the plan once (kernel-parameter copies on the batch's stream)
-    if ((rc = tc_enqueue_plan(b->plans.back(), true, b->own))) return fail(rc);
+    if ((rc = tc_upload_plan(b->plans.back(), b->own))) return fail(rc);
   }
-  if ((rc = cuda_error(cudaStreamSynchronize(b->own), "batch warm-up"))) return fail(rc);
+  if ((rc = cuda_error(cudaStreamSynchronize(b->own), "plan upload"))) return fail(rc);
   if (options & NMFA_BATCH_GRAPH) {
     if ((rc = cuda_error(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "capture"))) return fail(rc);
     rc = batch_enqueue(b, b->own);

@@ -144,6 +144,7 @@ struct TcPlan {
 int tc_pick_bn(int32_t replicas);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan);
+int tc_upload_plan(const TcPlan& plan, cudaStream_t st);
 int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st);
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,
               cudaStream_t st);
