@@ -35,6 +35,58 @@ int cuda_error(cudaError_t e, const char* where) {
   return set_error(NMFA_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+namespace {
+struct PoolState {
+  std::mutex mu;
+  cudaStream_t stream[128] = {};
+};
+PoolState& pool_state() {
+  static PoolState s;
+  return s;
+}
+// The current device's allocation stream; the first call on a device also tells
+// its default pool to keep freed memory.
+cudaStream_t pool_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  PoolState& ps = pool_state();
+  std::lock_guard<std::mutex> g(ps.mu);
+  if (ps.stream[dev] == nullptr) {
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    ps.stream[dev] = st;
+  }
+  return ps.stream[dev];
+}
+}  // namespace
+
+int pool_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  cudaStream_t st = pool_stream();
+  if (st == nullptr) return set_error(NMFA_ECUDA, "no allocation stream on this device");
+  cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    if (*p) cudaFreeAsync(*p, st);
+    *p = nullptr;
+    return cuda_error(e, "device allocation");
+  }
+  return NMFA_OK;
+}
+
+void pool_free(void* p, cudaEvent_t after) {
+  if (p == nullptr) return;
+  cudaStream_t st = pool_stream();
+  if (st == nullptr) return;
+  if (after != nullptr) cudaStreamWaitEvent(st, after, 0);
+  cudaFreeAsync(p, st);
+}
+
 }  // namespace nmfa
 
 using namespace nmfa;
@@ -92,11 +144,8 @@ namespace {
 int dev_alloc(nmfa_problem* p, void** out, size_t bytes) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(out, bytes);
-  if (e != cudaSuccess) {
-    *out = nullptr;
-    return cuda_error(e, "cudaMalloc");
-  }
+  const int rc = pool_alloc(out, bytes);
+  if (rc) return rc;
   p->allocations.push_back(*out);
   p->device_bytes += static_cast<int64_t>(bytes);
   return NMFA_OK;
@@ -110,18 +159,17 @@ int dev_alloc_t(nmfa_problem* p, T** out, size_t count) {
   return rc;
 }
 
-int ensure_buf(DevBuf& b, size_t bytes) {
+// Grows a scratch buffer; the old one is released once `after` (the completion of
+// the last run that may still use it, or nullptr) has completed.
+int ensure_buf(DevBuf& b, size_t bytes, cudaEvent_t after = nullptr) {
   if (b.bytes >= bytes && b.p != nullptr) return NMFA_OK;
   if (b.p != nullptr) {
-    cudaFree(b.p);
+    pool_free(b.p, after);
     b.p = nullptr;
     b.bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
-  if (e != cudaSuccess) {
-    b.p = nullptr;
-    return cuda_error(e, "scratch cudaMalloc");
-  }
+  const int rc = pool_alloc(&b.p, std::max<size_t>(bytes, 256));
+  if (rc) return rc;
   b.bytes = std::max<size_t>(bytes, 256);
   return NMFA_OK;
 }
@@ -390,10 +438,10 @@ int finish_create(nmfa_problem* p, const double* h, const HostCompact* hc = null
 void free_problem(nmfa_problem* p) {
   if (p == nullptr) return;
   if (p->done) cudaEventSynchronize(p->done);
-  for (void* a : p->allocations) cudaFree(a);
-  if (p->ws.p) cudaFree(p->ws.p);
-  if (p->io.p) cudaFree(p->io.p);
-  if (p->sign_scratch.p) cudaFree(p->sign_scratch.p);
+  for (void* a : p->allocations) pool_free(a);
+  pool_free(p->ws.p);
+  pool_free(p->io.p);
+  pool_free(p->sign_scratch.p);
   if (p->done) cudaEventDestroy(p->done);
   if (p->prof0) cudaEventDestroy(p->prof0);
   if (p->prof1) cudaEventDestroy(p->prof1);
@@ -494,7 +542,7 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
   if ((precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) && int8_ok) {
     auto it = std::find(p->allocations.begin(), p->allocations.end(), static_cast<void*>(p->J64));
     if (it != p->allocations.end()) {
-      cudaFree(p->J64);
+      pool_free(p->J64);
       p->allocations.erase(it);
       p->device_bytes -= static_cast<int64_t>(sizeof(double)) * n * n;
       p->J64 = nullptr;
@@ -646,7 +694,7 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
   // Runs on one handle share its scratch: order this run after the previous one.
   if ((rc = cuda_error(cudaStreamWaitEvent(st, p->done, 0), "stream wait"))) return rc;
   if (signs_dev == nullptr) {
-    if ((rc = ensure_buf(p->sign_scratch, static_cast<size_t>(replicas) * p->n))) return rc;
+    if ((rc = ensure_buf(p->sign_scratch, static_cast<size_t>(replicas) * p->n, p->done))) return rc;
     signs_dev = static_cast<int8_t*>(p->sign_scratch.p);
   }
   RunParams rp{};
@@ -691,7 +739,8 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
         pb.d = p->d64;
         pb.inv_d32 = p->inv_d32;
         if (!f64 && p->n >= kTiledF32MinN && p->replicas_per_cta == 0) {
-          if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas))))) return rc;
+          if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas)), p->done)))
+            return rc;
           rc = launch_dense_tiled_f32(pb, rp, static_cast<float*>(p->ws.p), st);
         } else {
           rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
@@ -713,7 +762,7 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
       if ((rc = tc_workspace_bytes(pb, replicas, &bytes))) return rc;
       // FP8-stored couplings are expanded to BF16 in front of the kernel's scratch
       const size_t jexp = p->precision == NMFA_BF16_FP8J ? static_cast<size_t>(p->n_pad) * p->n_pad * 2 : 0;
-      if ((rc = ensure_buf(p->ws, jexp + static_cast<size_t>(bytes)))) return rc;
+      if ((rc = ensure_buf(p->ws, jexp + static_cast<size_t>(bytes), p->done))) return rc;
       if (jexp) {
         if ((rc = launch_expand_e4m3_bf16(p->Jq, p->ws.p, static_cast<int64_t>(p->n_pad) * p->n_pad, st))) return rc;
         pb.Jq = p->ws.p;
@@ -893,11 +942,10 @@ static void free_batch(nmfa_batch* b) {
   if (b->done) cudaEventSynchronize(b->done);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (DevBuf& w : b->ws)
-    if (w.p) cudaFree(w.p);
-  if (b->signs.p) cudaFree(b->signs.p);
-  if (b->jexp.p) cudaFree(b->jexp.p);
-  if (b->status) cudaFree(b->status);
+  for (DevBuf& w : b->ws) pool_free(w.p);
+  pool_free(b->signs.p);
+  pool_free(b->jexp.p);
+  pool_free(b->status);
   if (b->done) cudaEventDestroy(b->done);
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
@@ -962,7 +1010,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
   if ((rc = cuda_error(cudaSetDevice(b->device), "cudaSetDevice"))) return fail(rc);
   if ((rc = cuda_error(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), "stream"))) return fail(rc);
   if ((rc = cuda_error(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event"))) return fail(rc);
-  if ((rc = cuda_error(cudaMalloc(&b->status, 4), "status"))) return fail(rc);
+  if ((rc = pool_alloc(reinterpret_cast<void**>(&b->status), 4))) return fail(rc);
   if ((rc = cuda_error(cudaMemset(b->status, 0, 4), "status"))) return fail(rc);
   size_t sign_bytes = 0;
   for (int32_t j = 0; j < count; ++j)
@@ -1137,8 +1185,8 @@ static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas) {
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   DevBuf ws;
-  bool okc = cudaMalloc(&T, sizeof(double) * t_f) == cudaSuccess &&
-             cudaMalloc(&signs, static_cast<size_t>(replicas) * p->n) == cudaSuccess &&
+  bool okc = pool_alloc(reinterpret_cast<void**>(&T), sizeof(double) * t_f) == NMFA_OK &&
+             pool_alloc(reinterpret_cast<void**>(&signs), static_cast<size_t>(replicas) * p->n) == NMFA_OK &&
              cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   if (okc) {
@@ -1178,9 +1226,9 @@ static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas) {
       best = bn;
     }
   }
-  if (ws.p) cudaFree(ws.p);
-  if (T) cudaFree(T);
-  if (signs) cudaFree(signs);
+  pool_free(ws.p);
+  pool_free(T);
+  pool_free(signs);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (st) cudaStreamDestroy(st);

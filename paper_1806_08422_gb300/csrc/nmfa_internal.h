@@ -19,6 +19,15 @@ inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_o
 int set_error(int code, const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);
 
+// Device memory of the library comes from the current device's stream-ordered pool,
+// which keeps freed memory for reuse: neither call synchronises the device (cudaFree
+// waits for all work on the device, which stalled a serving loop's launches behind
+// its releases).  pool_alloc returns memory usable on any stream.  pool_free releases
+// `p` once `after` (an event recorded after the buffer's last use, or nullptr when
+// the host has already seen that use complete) has completed.
+int pool_alloc(void** p, size_t bytes);
+void pool_free(void* p, cudaEvent_t after = nullptr);
+
 // Device-side status word written by kernels with bounded waits.
 enum DeviceStatus : int32_t { kStatusOk = 0, kStatusTimeout = 1 };
 

@@ -126,9 +126,9 @@ void reaper_main(nmfa_server* s) {
     for (nmfa_batch* b : dead) nmfa_batch_destroy(b);
     for (Request* r : batch) {
       if (r->prob) nmfa_destroy(r->prob);
-      if (r->T_dev) cudaFree(r->T_dev);
-      if (r->signs_dev) cudaFree(r->signs_dev);
-      if (r->energy_dev) cudaFree(r->energy_dev);
+      pool_free(r->T_dev);
+      pool_free(r->signs_dev);
+      pool_free(r->energy_dev);
       r->prob = nullptr;
       r->T_dev = nullptr;
       r->signs_dev = nullptr;
@@ -170,9 +170,10 @@ void loader_main(nmfa_server* s) {
     }
     int rc = nmfa_create(r->n, r->h.empty() ? nullptr : r->h.data(), r->J.data(), r->precision, &r->prob);
     if (rc == NMFA_OK) {
-      bool ok = cudaMalloc(&r->T_dev, sizeof(double) * std::max(r->t_f, 1)) == cudaSuccess &&
-                cudaMalloc(&r->signs_dev, static_cast<size_t>(r->replicas) * r->n) == cudaSuccess &&
-                cudaMalloc(&r->energy_dev, sizeof(double) * r->replicas) == cudaSuccess &&
+      bool ok = pool_alloc(reinterpret_cast<void**>(&r->T_dev), sizeof(double) * std::max(r->t_f, 1)) == NMFA_OK &&
+                pool_alloc(reinterpret_cast<void**>(&r->signs_dev), static_cast<size_t>(r->replicas) * r->n) ==
+                    NMFA_OK &&
+                pool_alloc(reinterpret_cast<void**>(&r->energy_dev), sizeof(double) * r->replicas) == NMFA_OK &&
                 cudaMemcpy(r->T_dev, r->T.data(), sizeof(double) * r->t_f, cudaMemcpyHostToDevice) == cudaSuccess;
       if (!ok) rc = NMFA_ENOMEM;
     }
@@ -426,9 +427,9 @@ void nmfa_server_destroy(nmfa_server* s) {
   for (auto& kv : s->all) {
     Request* r = kv.second;
     if (r->prob) nmfa_destroy(r->prob);
-    if (r->T_dev) cudaFree(r->T_dev);
-    if (r->signs_dev) cudaFree(r->signs_dev);
-    if (r->energy_dev) cudaFree(r->energy_dev);
+    pool_free(r->T_dev);
+    pool_free(r->signs_dev);
+    pool_free(r->energy_dev);
     delete r;
   }
   for (auto& st : s->streams) cudaStreamDestroy(st);
