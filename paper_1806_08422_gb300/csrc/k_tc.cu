@@ -518,6 +518,21 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           }
           if (++ks == KB) ks = 0;
         }
+        // The first claimed slot is the tile's own K slice: after the first step its S
+        // half is copied as soon as this tile has published, before the other row
+        // blocks have, so the step's first MMAs need not wait for the slowest tile.
+        const int early = (t > 0 && claimed > 0 && nb > 1) ? 1 : 0;
+        if (early) {  // (the copy is issued on abort too, so that the slot's barrier completes)
+          if (ok)
+            ok = wait_group_flags(gflags + b, 1, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
+                                  kTimeoutNs);
+          __syncwarp();
+          if (ok) ptx::fence_proxy_async_global();
+#pragma unroll
+          for (int a = 0; a < kAtoms; ++a)
+            ptx::tma_load_2d_warp(ring + claim_stage * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
+                                  kslice_base * kKSlot + a * kBK, sy, full0 + 8u * claim_stage);
+        }
         if (ok)
           ok = wait_group_flags(gflags, nb, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
                                 t == 0 ? kStartTimeoutNs : kTimeoutNs);
@@ -525,11 +540,16 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
         // those acquires before the elected lane's copies (memory ordering within the warp)
         __syncwarp();
         if (ok) ptx::fence_proxy_async_global();
-        // the S halves of the claimed slots (also on abort, so that their barriers complete)
+        // the S halves of the other claimed slots (also on abort, so that their
+        // barriers complete)
         {
           uint32_t st = claim_stage;
           int ks2 = kslice_base;
-          for (int kb = 0; kb < claimed; ++kb) {
+          if (early) {
+            if (++st == kStages) st = 0;
+            if (++ks2 == KB) ks2 = 0;
+          }
+          for (int kb = early; kb < claimed; ++kb) {
 #pragma unroll
             for (int a = 0; a < kAtoms; ++a)
               ptx::tma_load_2d_warp(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
