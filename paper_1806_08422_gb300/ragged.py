@@ -11,9 +11,14 @@ autotuner (`--tiles auto`), the default pick, or are 64 throughout.
     python -m paper_1806_08422_gb300.ragged [--count 512] [--replicas 64] [--reps 5]
 
 Prints one JSON line: spin-updates/s, the tensor work rate (2 n^2 R per step and
-instance at the 128-padded size the kernel computes, and at the unpadded size), and
-its fraction of the measured sustained BF16 peak.  This module only drives the C
-ABI; all annealing runs in the library's kernels.
+instance at the 128-padded size the kernel computes, and at the unpadded size) and
+its fraction of the measured BF16 peaks (burst: the launch is timed on its own;
+sustained beside it), and the memory view: the BF16 couplings the kernel reads
+(padded), the HBM bytes the batch needs at least (J once plus the outputs) and the
+rate at which the product consumes J (t_f passes over it, which would bound the
+batch at the measured HBM bandwidth if J were re-read from HBM every step; the
+kernel keeps each running tile's J block in L2 instead).  This module only drives
+the C ABI; all annealing runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -30,13 +35,15 @@ from . import nmfa
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def sustained_peak():
+def measured_peaks():
+    """(burst BF16 TFLOP/s, sustained BF16 TFLOP/s, HBM GB/s, source)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d.get("bf16_tflops_sustained", d.get("bf16_tflops"))), "measured"
+        return (float(d.get("bf16_tflops", d.get("bf16_tflops_sustained"))),
+                float(d.get("bf16_tflops_sustained", d.get("bf16_tflops"))), float(d["hbm_gbs"]), "measured")
     except Exception:
-        return 1700.0, "fallback"
+        return 1900.0, 1700.0, 6800.0, "fallback"
 
 
 def main():
@@ -88,7 +95,9 @@ def main():
     units = float(ns.sum()) * R * args.t_f
     flops_pad = 2.0 * float((npad ** 2).sum()) * R * (args.t_f + 1)
     flops = 2.0 * float((ns ** 2).sum()) * R * args.t_f
-    peak, kind = sustained_peak()
+    burst, sustained, hbm, kind = measured_peaks()
+    j_bytes = 2.0 * float((npad ** 2).sum())                  # BF16 J at the padded sizes
+    out_bytes = float(ns.sum()) * R + 8.0 * R * len(ns)     # int8 signs + int64 energies
     e0 = energies[0].cpu().numpy()
     out = {
         "workload": "%d instances, N uniform in [%d, %d] (half SK +-1, half G(N,0.5) max-cut), %d replicas each, "
@@ -98,8 +107,15 @@ def main():
         "spin_updates_per_s": units / per,
         "tensor_tflops_padded": flops_pad / per / 1e12,
         "tensor_tflops_unpadded": flops / per / 1e12,
-        "frac_of_sustained_bf16_padded": flops_pad / per / 1e12 / peak,
-        "peak_tflops": peak, "peak_source": kind + " bf16_tflops_sustained",
+        "frac_of_burst_bf16_padded": flops_pad / per / 1e12 / burst,
+        "frac_of_sustained_bf16_padded": flops_pad / per / 1e12 / sustained,
+        "peak_tflops_burst": burst, "peak_tflops_sustained": sustained, "peak_source": kind,
+        "j_bytes_bf16_padded": j_bytes,
+        "hbm_bytes_algorithmic": j_bytes + out_bytes,
+        "hbm_frac_algorithmic": (j_bytes + out_bytes) / per / 1e9 / hbm,
+        "j_consumption_gbs": j_bytes * (args.t_f + 1) / per / 1e9,
+        "j_consumption_over_hbm_peak": j_bytes * (args.t_f + 1) / per / 1e9 / hbm,
+        "hbm_gbs_peak": hbm,
         "tiles": args.tiles, "grid": info["grid"], "groups": info["groups"], "workspace_bytes": info["workspace_bytes"],
         "host_create_s": t_create, "batch_create_s": t_batch,
         "check_first_instance_min_energy": int(e0.min()),
