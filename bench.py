@@ -282,11 +282,20 @@ def main():
                     "peak_source": "%s bf16_tflops (burst)" % peak_kind,
                     "frac_of_sustained": achieved / sustained if sustained else None}
     else:
+        # CUDA-core path: FMA-bound; the denominator is this device's measured FMA rate
+        # (measured after the timed region, outside the launch count)
         achieved = flops / (kern_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
                     "traffic": None, "kernel_ms": kern_ms}
 
     extra = {}
+    alu = nmfa.nmfa_measure_alu_peaks(stream) if rank == 0 else None
+    if alu is not None:
+        extra["alu_peaks"] = dict(alu, source="measured by nmfa_measure_alu_peaks (FMA chains on every SM)")
+        if args.precision != "bf16":
+            pk = alu["fp64_fma_tflops" if args.precision == "fp64" else "fp32_fma_tflops"]
+            roofline.update({"peak": pk, "frac": achieved / pk,
+                             "peak_source": "measured %s FMA rate" % args.precision})
     if rank == 0 and not args.no_fp32_compare and args.precision != "fp32":
         # the plain FP32 per-instance CUDA-core path on the same workload
         p32 = nmfa.Problem(J, precision="fp32")
@@ -298,8 +307,12 @@ def main():
             p32.run_device(Td, SIGMA, ALPHA, REPLICAS, signs=signs, energy=energy, stream=stream)
             p32.sync()
             ms32.append(nmfa.nmfa_last_kernel_ms(p32.handle))
+        tf32 = 2.0 * N_SPINS * N_SPINS * REPLICAS * args.tf / (statistics.mean(ms32) / 1e3) / 1e12
         extra["fp32_path"] = {"value": units_per_step / (statistics.mean(ms32) / 1e3), "unit": "spin-updates/s",
-                              "kernel_ms": statistics.mean(ms32)}
+                              "kernel_ms": statistics.mean(ms32),
+                              "roofline": {"bound": "alu", "achieved": tf32, "unit": "TFLOP/s",
+                                           "peak": alu["fp32_fma_tflops"] if alu else None,
+                                           "frac": tf32 / alu["fp32_fma_tflops"] if alu else None}}
         p32.close()
 
     if rank == 0:

@@ -295,6 +295,15 @@ int nmfa_last_kernel_ms(nmfa_problem* p, float* ms);
  * 1, 2, 4 or 8).  Results do not depend on it. */
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t replicas_per_cta);
 
+/* Measured CUDA-core arithmetic peaks of the current device, the denominators of
+ * the CUDA-core paths' rooflines: out[0] = FP32 FMA throughput, out[1] = FP64 FMA
+ * throughput, both in TFLOP/s (2 flops per FMA), from dependent-chain FMA loops on
+ * every SM (eight chains per thread, 1024 threads per CTA, two CTAs per SM), the
+ * best of three timed launches on `cuda_stream` (NULL: the legacy default stream).
+ * `out` is host memory of 2 doubles.  Synchronous; takes a few tens of ms.
+ * Returns NMFA_EINVAL for a NULL `out`, NMFA_ECUDA on a CUDA error. */
+int nmfa_measure_alu_peaks(double* out, void* cuda_stream);
+
 /* Number of kernels this library has launched in this process so far. */
 uint64_t nmfa_launch_count(void);
 

@@ -826,6 +826,64 @@ int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int6
   return cuda_error(cudaGetLastError(), "conversion kernel launch");
 }
 
+// ---- CUDA-core arithmetic peaks --------------------------------------------------
+// Eight independent FMA chains per thread and 1024 threads per CTA keep every
+// scheduler's FMA pipe fed (8 warps x 8 chains per scheduler against a 4-cycle FP32
+// latency); the chains stay finite (a = 1 - 2^-20, b = 2^-20 pull x towards 1).
+// The result feeds a store the host never reads unless a chain reaches an
+// impossible value, so the loop cannot be removed.
+template <typename T>
+__global__ void __launch_bounds__(1024) fma_peak_kernel(T* sink, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = static_cast<T>(threadIdx.x + c) * static_cast<T>(1e-4);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    }
+  }
+  T acc = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc += x[c];
+  if (acc == static_cast<T>(-12345)) sink[0] = acc;
+}
+
+int measure_fma_peak(bool fp64, cudaStream_t st, double* tflops) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = 2 * sms, threads = 1024;
+  const int iters = fp64 ? 64 : 4096;  // ~10 ms at the respective rate
+  void* sink = nullptr;
+  int rc = pool_alloc(&sink, 16);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && rc == 0; ++rep) {
+    cudaEventRecord(e0, st);
+    if (fp64)
+      fma_peak_kernel<double><<<grid, threads, 0, st>>>(static_cast<double*>(sink), iters, 1.0 - 0x1p-20, 0x1p-20);
+    else
+      fma_peak_kernel<float><<<grid, threads, 0, st>>>(static_cast<float*>(sink), iters, 1.0f - 0x1p-20f, 0x1p-20f);
+    count_launch();
+    cudaEventRecord(e1, st);
+    rc = cuda_error(cudaEventSynchronize(e1), "peak kernel");
+    float ms = 0.0f;
+    if (rc == 0 && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pool_free(sink);
+  if (rc) return rc;
+  const double fmas = static_cast<double>(grid) * threads * iters * 16.0 * 8.0;
+  *tflops = 2.0 * fmas / (static_cast<double>(best) * 1e-3) / 1e12;
+  return NMFA_OK;
+}
+
 int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st) {
   convert_vec_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst, kind);
   count_launch();

@@ -653,6 +653,18 @@ int nmfa_profile_enable(nmfa_problem* p, int32_t on) {
   return NMFA_OK;
 }
 
+int nmfa_measure_alu_peaks(double* out, void* cuda_stream) {
+  if (out == nullptr) return set_error(NMFA_EINVAL, "out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double f32 = 0.0, f64 = 0.0;
+  int rc = measure_fma_peak(false, st, &f32);
+  if (rc == NMFA_OK) rc = measure_fma_peak(true, st, &f64);
+  if (rc) return rc;
+  out[0] = f32;
+  out[1] = f64;
+  return NMFA_OK;
+}
+
 int nmfa_last_kernel_ms(nmfa_problem* p, float* ms) {
   if (p == nullptr || ms == nullptr) return set_error(NMFA_EINVAL, "NULL argument");
   if (!p->prof_valid) return set_error(NMFA_EINVAL, "no profiled run");

@@ -58,6 +58,7 @@ SIGNATURES = {
     "nmfa_problem_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nmfa_profile_enable": (ctypes.c_int, [_P, _i32]),
     "nmfa_last_kernel_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "nmfa_measure_alu_peaks": (ctypes.c_int, [_P, _P]),
     "nmfa_tune_replicas_per_cta": (ctypes.c_int, [_P, _i32]),
     "nmfa_launch_count": (_u64, []),
     "nmfa_last_error": (ctypes.c_char_p, []),
@@ -187,6 +188,13 @@ def nmfa_last_kernel_ms(handle):
     ms = ctypes.c_float()
     _check(load().nmfa_last_kernel_ms(handle, ctypes.byref(ms)))
     return ms.value
+
+
+def nmfa_measure_alu_peaks(stream=None):
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    out = (ctypes.c_double * 2)()
+    _check(load().nmfa_measure_alu_peaks(ctypes.cast(out, ctypes.c_void_p), _stream_ptr(stream)))
+    return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1]}
 
 
 def nmfa_tune_replicas_per_cta(handle, rc):

@@ -117,3 +117,9 @@ def test_no_device_is_an_error_not_a_fallback(lib):
 def test_version_and_counter(lib):
     assert "sm_103a" in nmfa.nmfa_version()
     assert nmfa.nmfa_launch_count() >= 0
+
+
+def test_alu_peaks_rejects_null_output(lib):
+    # argument checking comes before any device work
+    assert lib.nmfa_measure_alu_peaks(None, None) == nmfa.NMFA_EINVAL
+    assert "NULL" in nmfa.nmfa_last_error()

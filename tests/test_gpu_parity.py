@@ -270,3 +270,12 @@ def test_full_c2_run_readout_and_energy():
     dens = out["energy_i64"].mean() / n ** 1.5
     assert -0.73 * 1.05 < dens < -0.73 * 0.95, dens
     g.close()
+
+
+def test_measured_alu_peaks_plausible():
+    # The CUDA-core paths' roofline denominators.  GB300: 152 SMs x 128 FP32 FMA lanes
+    # x 2.07 GHz bounds FP32 at 80.5 TFLOP/s; its FP64 rate is a small fraction of that.
+    from paper_1806_08422_gb300 import nmfa
+    pk = nmfa.nmfa_measure_alu_peaks()
+    assert 20.0 < pk["fp32_fma_tflops"] < 85.0, pk
+    assert 0.05 < pk["fp64_fma_tflops"] < pk["fp32_fma_tflops"] / 4, pk
