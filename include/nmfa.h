@@ -297,10 +297,11 @@ int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t replicas_per_cta);
 
 /* Measured CUDA-core arithmetic peaks of the current device, the denominators of
  * the CUDA-core paths' rooflines: out[0] = FP32 FMA throughput, out[1] = FP64 FMA
- * throughput, both in TFLOP/s (2 flops per FMA), from dependent-chain FMA loops on
- * every SM (eight chains per thread, 1024 threads per CTA, two CTAs per SM), the
- * best of three timed launches on `cuda_stream` (NULL: the legacy default stream).
- * `out` is host memory of 2 doubles.  Synchronous; takes a few tens of ms.
+ * throughput, both in TFLOP/s (2 flops per FMA), out[2] = tanh.approx.f32 throughput
+ * of the MUFU in Tops/s; from dependent-chain loops on every SM (eight chains per
+ * thread, 1024 threads per CTA, two CTAs per SM), the best of three timed launches
+ * each on `cuda_stream` (NULL: the legacy default stream).  `out` is host memory of
+ * 3 doubles.  Synchronous; takes a few tens of ms.
  * Returns NMFA_EINVAL for a NULL `out`, NMFA_ECUDA on a CUDA error. */
 int nmfa_measure_alu_peaks(double* out, void* cuda_stream);
 

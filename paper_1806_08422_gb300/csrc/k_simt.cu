@@ -850,12 +850,32 @@ __global__ void __launch_bounds__(1024) fma_peak_kernel(T* sink, int iters, T a,
   if (acc == static_cast<T>(-12345)) sink[0] = acc;
 }
 
-int measure_fma_peak(bool fp64, cudaStream_t st, double* tflops) {
+// Eight independent chains of tanh.approx.f32 per thread (the MUFU op of the tensor
+// path's epilogue): x -> tanh(x) shrinks towards 0 and stays finite.
+__global__ void __launch_bounds__(1024) mufu_peak_kernel(float* sink, int iters) {
+  float x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = 0.5f + 1e-4f * static_cast<float>(threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) asm volatile("tanh.approx.f32 %0, %0;" : "+f"(x[c]));
+    }
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc += x[c];
+  if (acc == -12345.0f) sink[0] = acc;
+}
+
+// kind 0: FP32 FMA, 1: FP64 FMA (TFLOP/s, 2 flops per FMA); 2: MUFU tanh (Tops/s).
+int measure_alu_peak(int kind, cudaStream_t st, double* rate) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = 2 * sms, threads = 1024;
-  const int iters = fp64 ? 64 : 4096;  // ~10 ms at the respective rate
+  const int iters = kind == 1 ? 64 : kind == 2 ? 256 : 4096;  // a few ms at the respective rate
   void* sink = nullptr;
   int rc = pool_alloc(&sink, 16);
   if (rc) return rc;
@@ -865,8 +885,10 @@ int measure_fma_peak(bool fp64, cudaStream_t st, double* tflops) {
   float best = 1e30f;
   for (int rep = 0; rep < 4 && rc == 0; ++rep) {
     cudaEventRecord(e0, st);
-    if (fp64)
+    if (kind == 1)
       fma_peak_kernel<double><<<grid, threads, 0, st>>>(static_cast<double*>(sink), iters, 1.0 - 0x1p-20, 0x1p-20);
+    else if (kind == 2)
+      mufu_peak_kernel<<<grid, threads, 0, st>>>(static_cast<float*>(sink), iters);
     else
       fma_peak_kernel<float><<<grid, threads, 0, st>>>(static_cast<float*>(sink), iters, 1.0f - 0x1p-20f, 0x1p-20f);
     count_launch();
@@ -879,8 +901,8 @@ int measure_fma_peak(bool fp64, cudaStream_t st, double* tflops) {
   cudaEventDestroy(e1);
   pool_free(sink);
   if (rc) return rc;
-  const double fmas = static_cast<double>(grid) * threads * iters * 16.0 * 8.0;
-  *tflops = 2.0 * fmas / (static_cast<double>(best) * 1e-3) / 1e12;
+  const double ops = static_cast<double>(grid) * threads * iters * 16.0 * 8.0;
+  *rate = (kind == 2 ? 1.0 : 2.0) * ops / (static_cast<double>(best) * 1e-3) / 1e12;
   return NMFA_OK;
 }
 

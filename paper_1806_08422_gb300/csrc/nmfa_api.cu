@@ -656,12 +656,12 @@ int nmfa_profile_enable(nmfa_problem* p, int32_t on) {
 int nmfa_measure_alu_peaks(double* out, void* cuda_stream) {
   if (out == nullptr) return set_error(NMFA_EINVAL, "out is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  double f32 = 0.0, f64 = 0.0;
-  int rc = measure_fma_peak(false, st, &f32);
-  if (rc == NMFA_OK) rc = measure_fma_peak(true, st, &f64);
-  if (rc) return rc;
-  out[0] = f32;
-  out[1] = f64;
+  double r[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) {
+    const int rc = measure_alu_peak(k, st, &r[k]);
+    if (rc) return rc;
+  }
+  for (int k = 0; k < 3; ++k) out[k] = r[k];
   return NMFA_OK;
 }
 

@@ -84,9 +84,10 @@ struct CsrProblem {
 int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,
                int replicas_per_cta);
 
-// FP32 (fp64 = false) or FP64 FMA throughput of the current device in TFLOP/s
-// (2 flops per FMA), timed with CUDA events on `st`; synchronous.
-int measure_fma_peak(bool fp64, cudaStream_t st, double* tflops);
+// Arithmetic throughput of the current device, timed with CUDA events on `st`
+// (synchronous): kind 0 = FP32 FMA, 1 = FP64 FMA (TFLOP/s, 2 flops per FMA),
+// 2 = tanh.approx.f32 on the MUFU (Tops/s).
+int measure_alu_peak(int kind, cudaStream_t st, double* rate);
 
 // ---- Eq. (1) energies from signs --------------------------------------------
 struct EnergyProblem {

@@ -191,10 +191,11 @@ def nmfa_last_kernel_ms(handle):
 
 
 def nmfa_measure_alu_peaks(stream=None):
-    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
-    out = (ctypes.c_double * 2)()
+    """Measured FP32 and FP64 FMA throughput (TFLOP/s) and MUFU tanh throughput
+    (Tops/s) of the current device."""
+    out = (ctypes.c_double * 3)()
     _check(load().nmfa_measure_alu_peaks(ctypes.cast(out, ctypes.c_void_p), _stream_ptr(stream)))
-    return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1]}
+    return {"fp32_fma_tflops": out[0], "fp64_fma_tflops": out[1], "mufu_tanh_tops": out[2]}
 
 
 def nmfa_tune_replicas_per_cta(handle, rc):

@@ -279,3 +279,5 @@ def test_measured_alu_peaks_plausible():
     pk = nmfa.nmfa_measure_alu_peaks()
     assert 20.0 < pk["fp32_fma_tflops"] < 85.0, pk
     assert 0.05 < pk["fp64_fma_tflops"] < pk["fp32_fma_tflops"] / 4, pk
+    # 16 MUFU lanes per SM: 5.03 Tops/s at 2.07 GHz
+    assert 1.0 < pk["mufu_tanh_tops"] < 5.5, pk
