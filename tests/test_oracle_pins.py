@@ -125,6 +125,26 @@ def test_state_bound():
 
 
 # --------------------------------------------------------------------------
+# High temperature (Algorithm 1 with T_t huge): |tanh x| <= |x| and, by
+# Cauchy-Schwarz, (|h_i| + sum_j |J_ij| |s_j|) / d_i <= sqrt(n) for |s_j| <= 1, so
+# |Phi_i| <= sqrt(n) + sigma |z| and every state stays below (sqrt(n) + sigma z_max) / T
+# (the uniforms of the stream are >= 2^-24, so |z| <= sqrt(48 ln 2)).  The state is
+# O(1/T): it shrinks tenfold when T grows tenfold.
+# --------------------------------------------------------------------------
+def test_high_temperature_state_is_order_one_over_T():
+    n, R, tf, sigma = 40, 6, 30, 0.15
+    J = inst.sk(n, 21)
+    h = inst.random_fields(n, 0.5, 22)
+    zmax = np.sqrt(48.0 * np.log(2.0))
+    peaks = []
+    for Tval in (1e4, 1e5, 1e6):
+        st = oracle.run(J, [Tval] * tf, sigma, 0.15, R, seed=4, h=h, want_state=True)["state"]
+        assert np.all(np.abs(st) <= (np.sqrt(n) + sigma * zmax) / Tval)
+        peaks.append(np.abs(st).max())
+    assert 9.0 < peaks[0] / peaks[1] < 11.0 and 9.0 < peaks[1] / peaks[2] < 11.0
+
+
+# --------------------------------------------------------------------------
 # Spin-flip symmetry at h = 0: negating every noise draw negates the whole
 # trajectory exactly (tanh odd, coupling linear, IEEE negation exact), so the
 # signs flip and Eq. (1) is unchanged.
