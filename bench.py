@@ -141,6 +141,17 @@ def cpu_baseline(sample_replicas=48, sample_steps=T_F, nthreads=0):
                       % (N_SPINS, sample_replicas, sample_steps, T_F, dt)}
 
 
+def bench_config(precision, tf, ws):
+    """The workload both arms name: the bench's run of Algorithm 1."""
+    return {"workload": "SK N=2000 J=+-1 h=0, 1024 replicas, t_f=1000, sigma=alpha=0.15, "
+                        "default 3-segment schedule; %s" % (
+                            "BF16 J/S, FP32 accumulation on tcgen05" if precision == "bf16"
+                            else precision + " CUDA-core path"),
+            "n": N_SPINS, "replicas_per_gpu": REPLICAS, "t_f": tf,
+            "l2": "flushed between timed steps (256 MB write, outside the step events)",
+            "parallelism": "replicas" if ws == 1 else "replicas x%d ranks" % ws}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -158,10 +169,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "SK N=2000 +-1, h=0, sigma=alpha=0.15, default schedule; each step a bounded "
-                                   "sample: 16 replicas x 200 steps of the 1024-replica, 1000-step run"},
+            "config": bench_config(args.precision, args.tf, ws),
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "16 replicas x 200 steps per bench step"},
+                             "sample": "FP64 C oracle, OpenMP over replicas; each bench step a bounded sample of "
+                                       "the workload: 16 of its 1024 replicas over the first 200 of its 1000 "
+                                       "steps"},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -320,13 +332,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": "SK N=2000 J=+-1 h=0, 1024 replicas, t_f=1000, sigma=alpha=0.15, "
-                                       "default 3-segment schedule; %s" % (
-                                           "BF16 J/S, FP32 accumulation on tcgen05" if args.precision == "bf16"
-                                           else args.precision + " CUDA-core path"),
-                           "n": N_SPINS, "replicas_per_gpu": REPLICAS, "t_f": args.tf,
-                           "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                           "parallelism": "replicas" if ws == 1 else "replicas x%d ranks" % ws},
+                "config": bench_config(args.precision, args.tf, ws),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "wall_s_timed": t_wall, "step_ms": step_ms}
         line.update(extra)
