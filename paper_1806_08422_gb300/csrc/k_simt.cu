@@ -224,11 +224,17 @@ dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
 
 // CSR: coupling sums run over the stored entries of row i in stored order.
 // CSR rows are short (degree 3 for the sparse MAX-CUT classes), so a thread's work per
-// spin is mostly the noise draw and tanh; twice the threads of the dense kernel give
-// the SM more warps to hide their latency.
+// spin is mostly the noise draw and tanh; two or four times the threads of the dense
+// kernel give the SM more warps to hide their latency.  NT threads per CTA: 1024 for
+// FP32 problems of n >= 768 spins (measured on GB300, 512 replicas, 1000 steps: n = 1000
+// 2.35 -> 2.31 ms, n = 2000 4.69 -> 4.15 ms), 512 otherwise (a 1024-thread CTA is slower for small n, whose
+// rows leave most warps idle at every step's barrier, and for FP64, whose kernel
+// needs more than the 64 registers a thread may then hold).
 constexpr int kCsrThreads = 512;
-template <typename T, int RC, typename VT>
-__global__ void __launch_bounds__(kCsrThreads)
+constexpr int kCsrThreadsWide = 1024;
+constexpr int kCsrWideMinN = 768;
+template <typename T, int RC, typename VT, int NT>
+__global__ void __launch_bounds__(NT)
 csr_kernel(CsrProblem pb, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = pb.n;
@@ -423,15 +429,25 @@ int launch_csr_rc(const CsrProblem& pb, const RunParams& rp, cudaStream_t st) {
   if (state_bytes > static_cast<size_t>(max_smem_optin()))
     return set_error(NMFA_EUNSUPPORTED, "CSR path: state of n spins does not fit in shared memory");
   const int grid = (rp.replicas + RC - 1) / RC;
-  if (pb.val_int8) {
-    auto k = csr_kernel<T, RC, int8_t>;
+  const bool wide = sizeof(T) == 4 && pb.n >= kCsrWideMinN;
+  auto go = [&](auto k, int threads) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
-    k<<<grid, kCsrThreads, state_bytes, st>>>(pb, rp);
-  } else {
-    auto k = csr_kernel<T, RC, T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(state_bytes));
-    k<<<grid, kCsrThreads, state_bytes, st>>>(pb, rp);
+    k<<<grid, threads, state_bytes, st>>>(pb, rp);
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (wide) {
+      if (pb.val_int8)
+        go(csr_kernel<T, RC, int8_t, kCsrThreadsWide>, kCsrThreadsWide);
+      else
+        go(csr_kernel<T, RC, T, kCsrThreadsWide>, kCsrThreadsWide);
+      count_launch();
+      return cuda_error(cudaGetLastError(), "CSR kernel launch");
+    }
   }
+  if (pb.val_int8)
+    go(csr_kernel<T, RC, int8_t, kCsrThreads>, kCsrThreads);
+  else
+    go(csr_kernel<T, RC, T, kCsrThreads>, kCsrThreads);
   count_launch();
   return cuda_error(cudaGetLastError(), "CSR kernel launch");
 }
@@ -451,7 +467,7 @@ int pick_rc(int n, int replicas, size_t elem, int requested) {
   return rc;
 }
 
-// Replica block of the CSR kernel.  A thread works through ceil(n / kCsrThreads)
+// Replica block of the CSR kernel.  A thread works through ceil(n / threads)
 // spins per step, and each Philox call serves four replicas, so wide blocks pay off
 // once the rows fill much of the CTA; small n wants more CTAs (measured on GB300,
 // FP32, 512 replicas, ms per 1000-step run: n = 100: 0.94 / 0.76 / 0.99 for 1 / 2 / 4
@@ -464,7 +480,7 @@ int pick_rc_csr(int n, int replicas, size_t elem, int requested) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t limit = static_cast<size_t>(max_smem_optin());
-  int rc = n < kCsrThreads / 2 ? 2 : 4;
+  int rc = n < 256 ? 2 : 4;
   while (rc > 1 && 2ull * n * rc * elem > limit) rc >>= 1;
   while (rc > 1 && 5 * ((replicas + rc - 1) / rc) < 4 * sms) rc >>= 1;
   return rc;
