@@ -162,7 +162,8 @@ def test_zero_state_and_state_bound(prec):
 # ---------------------------------------------------------------- sparse path
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_csr_single_step(prec):
-    for J in (inst.moebius(400), inst.regular3(300, 3)):
+    # n = 1000 takes the 1024-thread CTA of the FP32 CSR kernel (n >= 768)
+    for J in (inst.moebius(400), inst.regular3(300, 3), inst.moebius(1000)):
         n, R = J.shape[0], 48
         csr = inst.to_csr(J)
         h = inst.random_fields(n, 0.4, 17)
@@ -174,6 +175,27 @@ def test_csr_single_step(prec):
         err = np.abs(out["phi"] - ref["phi"]) / scale
         assert err.max() <= TOL[prec]
         g.close()
+
+
+def test_csr_full_size_sampled():
+    # The sparse workload's launch configuration (Moebius N = 2000, 512 replicas:
+    # 4 replicas and 1024 threads per CTA, 128 CTAs); sampled replica slices against
+    # the oracle, one step from a random state with fields.
+    J = inst.moebius(2000)
+    n, R = 2000, 512
+    csr = inst.to_csr(J)
+    h = inst.random_fields(n, 0.4, 23)
+    s0 = _rand_state(R, n, 24)
+    g = Gpu(None, h=h, precision="fp32", csr=csr, n=n)
+    out = g.run([0.8], 0.15, 0.15, R, seed=6, stream_id=2, s0=s0, want_phi=True)
+    for r0 in (0, 254, R - 6):
+        sl = slice(r0, r0 + 6)
+        ref = oracle.run(None, [0.8], 0.15, 0.15, 6, seed=6, stream=2, h=h, s0=s0[sl], want_phi=True, csr=csr,
+                         r_first=r0)
+        scale = phi_scale(J, s0[sl], h, 0.15, 6, 2, r_first=r0)
+        err = np.abs(out["phi"][sl] - ref["phi"]) / scale
+        assert err.max() <= TOL["fp32"], (r0, float(err.max()))
+    g.close()
 
 
 def test_csr_sigma0_fp64_trajectory_and_energy():
