@@ -1072,7 +1072,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     b->energy_fused.push_back(tc_fuses_energy(t.pb, t.rp) ? 1 : 0);
     t.bn = (options & NMFA_BATCH_BN64) ? 64
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
-                                             : tc_pick_bn(jb.replicas);
+                                             : tc_pick_bn(jb.replicas, p->n_pad);
     b->bn.push_back(t.bn);
   }
   for (int bnv : {128, 64}) {
@@ -1182,14 +1182,14 @@ static std::mutex g_tune_mu;
 static std::map<std::pair<int, int>, int> g_tune_cache;
 
 static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas) {
-  if (replicas <= 64 || p->precision != NMFA_BF16) return tc_pick_bn(replicas);
+  if (replicas <= 64 || p->precision != NMFA_BF16) return tc_pick_bn(replicas, p->n_pad);
   const std::pair<int, int> key(p->n_pad, replicas);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) return it->second;
   }
-  int best = tc_pick_bn(replicas);
+  int best = tc_pick_bn(replicas, p->n_pad);
   float best_ms = 1e30f;
   const int t_f = 24;
   double* T = nullptr;

@@ -155,7 +155,8 @@ struct TcPlan {
   int32_t* status = nullptr;
   double makespan = 0.0;             // scheduler's estimate (relative units)
 };
-int tc_pick_bn(int32_t replicas);
+// Default replicas per tile (64 or 128) of a run of `replicas` replicas of an n_pad problem.
+int tc_pick_bn(int32_t replicas, int32_t n_pad);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan);
 int tc_upload_plan(const TcPlan& plan, cudaStream_t st);
