@@ -38,36 +38,51 @@ int cuda_error(cudaError_t e, const char* where) {
 namespace {
 struct PoolState {
   std::mutex mu;
-  cudaStream_t stream[128] = {};
+  cudaStream_t alloc_stream[128] = {};
+  cudaStream_t free_stream[128] = {};
 };
 PoolState& pool_state() {
   static PoolState s;
   return s;
 }
-// The current device's allocation stream; the first call on a device also tells
-// its default pool to keep freed memory.
-cudaStream_t pool_stream() {
+// The current device's allocation stream (free = false) or release stream (true).
+// Allocations and releases use separate streams: a release waits for the run that
+// last used the buffer, and an allocation synchronises its own stream, so sharing
+// one stream would make allocations wait for other runs.  The pool still hands a
+// released block to a later allocation on the other stream once the release has
+// executed.  The first call on a device also tells its default pool to keep freed
+// memory and never to make an allocation wait for a pending release.
+cudaStream_t pool_stream(bool free) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
   PoolState& ps = pool_state();
   std::lock_guard<std::mutex> g(ps.mu);
-  if (ps.stream[dev] == nullptr) {
+  if (ps.alloc_stream[dev] == nullptr) {
     cudaMemPool_t pool = nullptr;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t keep = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      // never make an allocation wait for a pending release (it would wait for the
+      // run the release waits for); reuse released blocks once they are free
+      int no = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    ps.stream[dev] = st;
+    cudaStream_t a = nullptr, f = nullptr;
+    if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamDestroy(a);
+      return nullptr;
+    }
+    ps.alloc_stream[dev] = a;
+    ps.free_stream[dev] = f;
   }
-  return ps.stream[dev];
+  return free ? ps.free_stream[dev] : ps.alloc_stream[dev];
 }
 }  // namespace
 
 int pool_alloc(void** p, size_t bytes) {
   *p = nullptr;
-  cudaStream_t st = pool_stream();
+  cudaStream_t st = pool_stream(false);
   if (st == nullptr) return set_error(NMFA_ECUDA, "no allocation stream on this device");
   cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -81,7 +96,7 @@ int pool_alloc(void** p, size_t bytes) {
 
 void pool_free(void* p, cudaEvent_t after) {
   if (p == nullptr) return;
-  cudaStream_t st = pool_stream();
+  cudaStream_t st = pool_stream(true);
   if (st == nullptr) return;
   if (after != nullptr) cudaStreamWaitEvent(st, after, 0);
   cudaFreeAsync(p, st);
