@@ -622,13 +622,17 @@ int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_
 // problems are summed exactly (int32 row sums, int64 totals); real-valued ones
 // in FP64.  One CTA per block of kEnergyReps replicas.
 // ----------------------------------------------------------------------------
-constexpr int kEnergyReps = 8;
+// Replicas per CTA of the energy kernels: 8, or fewer when the sign block of 8
+// replicas (8 n bytes) would not fit in shared memory.  The per-replica sums do not
+// depend on it.
+constexpr int kEnergyRepsMax = 8;
 constexpr int kEnergyThreads = 256;
 
 __device__ __forceinline__ int dp4a_s8(int a, int b, int c) { return __dp4a(a, b, c); }
 
 // Integer J (int8, rows padded to ld8 bytes, a multiple of 16): one warp per row
 // i, lanes stride over j in 16-byte words, dp4a products.
+template <int kEnergyReps>
 __global__ void __launch_bounds__(kEnergyThreads)
 energy_int8_kernel(int n, int ld8, const int8_t* __restrict__ J8, const double* __restrict__ h,
                    const int8_t* __restrict__ signs, int R, double* E, long long* Ei64) {
@@ -691,6 +695,7 @@ energy_int8_kernel(int n, int ld8, const int8_t* __restrict__ J8, const double* 
 }
 
 // Real-valued (or wide-integer) J in FP64; thread per row i, j ascending, or CSR.
+template <int kEnergyReps>
 __global__ void __launch_bounds__(kEnergyThreads)
 energy_f64_kernel(int n, const double* __restrict__ J64, const int32_t* __restrict__ row_ptr,
                   const int32_t* __restrict__ col, const double* __restrict__ val,
@@ -747,26 +752,42 @@ energy_f64_kernel(int n, const double* __restrict__ J64, const int32_t* __restri
   }
 }
 
+template <int REPS>
+void launch_energy_reps(const EnergyProblem& ep, const int8_t* signs, int32_t replicas, double* energy,
+                        int64_t* energy_i64, size_t smem, cudaStream_t st) {
+  const int grid = (replicas + REPS - 1) / REPS;
+  if (ep.J8 != nullptr) {
+    const int ld8 = (ep.n + 15) / 16 * 16;
+    cudaFuncSetAttribute(energy_int8_kernel<REPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    energy_int8_kernel<REPS><<<grid, kEnergyThreads, smem, st>>>(
+        ep.n, ld8, ep.J8, ep.h, signs, replicas, energy, reinterpret_cast<long long*>(energy_i64));
+  } else {
+    cudaFuncSetAttribute(energy_f64_kernel<REPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    energy_f64_kernel<REPS><<<grid, kEnergyThreads, smem, st>>>(
+        ep.n, ep.J64, ep.row_ptr, ep.col, ep.val64, ep.h, signs, replicas,
+        ep.integer_valued ? 1 : 0, energy, reinterpret_cast<long long*>(energy_i64));
+  }
+}
+
 int launch_energy(const EnergyProblem& ep, const int8_t* signs, int32_t replicas, double* energy,
                   int64_t* energy_i64, cudaStream_t st) {
   if (energy == nullptr && energy_i64 == nullptr) return NMFA_OK;
-  const int grid = (replicas + kEnergyReps - 1) / kEnergyReps;
-  if (ep.J8 != nullptr) {
-    const int ld8 = (ep.n + 15) / 16 * 16;
-    const size_t smem = static_cast<size_t>(kEnergyReps) * ld8;
-    if (smem > static_cast<size_t>(max_smem_optin()))
-      return set_error(NMFA_EUNSUPPORTED, "energy kernel: sign block does not fit in shared memory");
-    cudaFuncSetAttribute(energy_int8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    energy_int8_kernel<<<grid, kEnergyThreads, smem, st>>>(
-        ep.n, ld8, ep.J8, ep.h, signs, replicas, energy, reinterpret_cast<long long*>(energy_i64));
-  } else {
-    const size_t smem = static_cast<size_t>(kEnergyReps) * ep.n;
-    if (smem > static_cast<size_t>(max_smem_optin()) - static_cast<size_t>(kEnergyThreads) * kEnergyReps * 8)
-      return set_error(NMFA_EUNSUPPORTED, "energy kernel: sign block does not fit in shared memory");
-    cudaFuncSetAttribute(energy_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    energy_f64_kernel<<<grid, kEnergyThreads, smem, st>>>(
-        ep.n, ep.J64, ep.row_ptr, ep.col, ep.val64, ep.h, signs, replicas,
-        ep.integer_valued ? 1 : 0, energy, reinterpret_cast<long long*>(energy_i64));
+  const size_t limit = static_cast<size_t>(max_smem_optin());
+  const size_t row = ep.J8 != nullptr ? static_cast<size_t>((ep.n + 15) / 16 * 16) : static_cast<size_t>(ep.n);
+  int reps = kEnergyRepsMax;
+  auto fits = [&](int r) {
+    // dynamic sign block plus the kernel's static partial sums
+    const size_t stat = static_cast<size_t>(ep.J8 != nullptr ? kEnergyThreads / 32 : kEnergyThreads) * r * 8;
+    return static_cast<size_t>(r) * row + stat <= limit;
+  };
+  while (reps > 1 && !fits(reps)) reps >>= 1;
+  if (!fits(reps)) return set_error(NMFA_EUNSUPPORTED, "energy kernel: sign block does not fit in shared memory");
+  const size_t smem = static_cast<size_t>(reps) * row;
+  switch (reps) {
+    case 8: launch_energy_reps<8>(ep, signs, replicas, energy, energy_i64, smem, st); break;
+    case 4: launch_energy_reps<4>(ep, signs, replicas, energy, energy_i64, smem, st); break;
+    case 2: launch_energy_reps<2>(ep, signs, replicas, energy, energy_i64, smem, st); break;
+    default: launch_energy_reps<1>(ep, signs, replicas, energy, energy_i64, smem, st); break;
   }
   count_launch();
   return cuda_error(cudaGetLastError(), "energy kernel launch");

@@ -120,7 +120,20 @@ def to_csr(J: np.ndarray):
 
 
 def moebius_csr(n: int):
-    return to_csr(moebius(n))
+    """The Moebius ladder of `moebius(n)` built directly in CSR form (no dense
+    matrix, so it serves sizes whose n x n array would not fit in memory)."""
+    if n % 2 or n < 4:
+        raise ValueError("Moebius ladder needs an even n >= 4")
+    i = np.arange(n)
+    nbr = np.stack([(i - 1) % n, (i + 1) % n, (i + n // 2) % n], axis=1)
+    nbr.sort(axis=1)
+    if n == 4:  # K_4: the chords coincide with ring edges; keep each neighbour once
+        rows = [np.unique(r) for r in nbr]
+        row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+        col = np.concatenate(rows).astype(np.int32)
+        return row_ptr, col, np.ones(len(col), dtype=np.float64)
+    row_ptr = np.arange(0, 3 * n + 1, 3, dtype=np.int64)
+    return row_ptr, nbr.reshape(-1).astype(np.int32), np.ones(3 * n, dtype=np.float64)
 
 
 # ----------------------------------------------------------------------------

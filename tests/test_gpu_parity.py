@@ -198,6 +198,42 @@ def test_csr_full_size_sampled():
     g.close()
 
 
+def test_csr_largest_state_that_fits():
+    # The CSR kernels keep their replica block's whole state in shared memory (two
+    # FP32 copies per replica).  At one replica per CTA that holds n = opt-in
+    # shared memory / 8 spins: a ladder of that size must match the oracle, and one
+    # of the next even size must be rejected with NMFA_EUNSUPPORTED, not fault.
+    import torch
+    from paper_1806_08422_gb300 import nmfa
+    props = torch.cuda.get_device_properties(0)
+    limit = getattr(props, "shared_memory_per_block_optin", None)
+    if not limit:
+        pytest.skip("opt-in shared memory size not reported by this torch")
+    n = (limit // 8) // 2 * 2
+    csr = inst.moebius_csr(n)
+    R = 3
+    s0 = _rand_state(R, n, 25)
+    ref = oracle.run(None, [0.7], 0.15, 0.15, R, seed=8, s0=s0, want_phi=True, csr=csr)
+    g = Gpu(None, precision="fp32", csr=csr, n=n)
+    out = g.run([0.7], 0.15, 0.15, R, seed=8, s0=s0, want_phi=True)
+    rows = np.repeat(np.arange(n), 3)
+    Jsp = (rows, csr[1], csr[2])
+    z = np.array([[oracle.gauss(8, 0, r, 0, i) for i in range(n)] for r in range(R)])
+    d = np.sqrt(3.0)
+    scale = np.zeros((R, n))
+    for r in range(R):
+        np.add.at(scale[r], rows, np.abs(csr[2] * s0[r][csr[1]]))
+    scale = scale / d + 0.15 * np.abs(z)
+    assert (np.abs(out["phi"] - ref["phi"]) / scale).max() <= TOL["fp32"]
+    g.close()
+    big = inst.moebius_csr(n + 2)
+    g = Gpu(None, precision="fp32", csr=big, n=n + 2)
+    with pytest.raises(nmfa.NmfaError) as ei:
+        g.run([0.7], 0.15, 0.15, 1, seed=8)
+    assert ei.value.code == nmfa.NMFA_EUNSUPPORTED
+    g.close()
+
+
 def test_csr_sigma0_fp64_trajectory_and_energy():
     J = inst.moebius(100)
     n, R = 100, 8

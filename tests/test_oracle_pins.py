@@ -333,6 +333,13 @@ def test_csr_equals_dense():
     np.testing.assert_array_equal(a["energy_i64"], b["energy_i64"])
 
 
+def test_moebius_csr_generator_matches_dense_ladder():
+    # the direct CSR construction (used for ladders too large for a dense matrix)
+    for n in (4, 6, 16, 100, 2000):
+        for x, y in zip(inst.moebius_csr(n), inst.to_csr(inst.moebius(n))):
+            np.testing.assert_array_equal(x, y)
+
+
 # --------------------------------------------------------------------------
 # Fig. 3 (qualitative, no numbers survive): a 16-spin Moebius ladder with the
 # schedule compressed to 100 steps; spins leave 0, saturate near +-1 and the
