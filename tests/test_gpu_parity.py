@@ -313,6 +313,50 @@ def test_tensor_two_waves():
     g.close()
 
 
+def _hashed_pm1(n, salt):
+    # a symmetric +-1 instance with zero diagonal built block by block (no n x n
+    # temporaries beyond the result): J_ij = +-1 from a hash of (min(i,j), max(i,j))
+    J = np.empty((n, n), dtype=np.float64)
+    j = np.arange(n, dtype=np.uint64)
+    for i0 in range(0, n, 512):
+        i = np.arange(i0, min(i0 + 512, n), dtype=np.uint64)[:, None]
+        lo, hi = np.minimum(i, j), np.maximum(i, j)
+        hsh = (lo * np.uint64(0x9E3779B97F4A7C15) ^ hi * np.uint64(0xC2B2AE3D27D4EB4F) ^ np.uint64(salt))
+        hsh ^= hsh >> np.uint64(29)
+        J[i0:i0 + len(i)] = np.where((hsh * np.uint64(0xBF58476D1CE4E5B9)) >> np.uint64(63), 1.0, -1.0)
+    np.fill_diagonal(J, 0.0)
+    return J
+
+
+def test_tensor_largest_group():
+    # A group's row-block tiles must all be co-resident: with 128-replica tiles and
+    # one CTA per SM that is n_pad / 128 <= SMs (n = 19,456 on a 152-SM GB300).
+    # The largest such problem runs one step on every SM and matches the oracle on
+    # sampled replicas; one more row block is rejected with NMFA_EUNSUPPORTED.
+    # (Host memory: two n x n binary64 matrices of about 3 GB.)
+    import torch
+    from paper_1806_08422_gb300 import nmfa
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n, R = 128 * sms, 128
+    J = _hashed_pm1(n, 7)
+    s0 = _rand_state(R, n, 27)
+    g = Gpu(J, precision="bf16")
+    out = g.run([1.2], 0.15, 0.15, R, seed=2, s0=s0, want_phi=True, want_energy=False)
+    g.close()
+    for r0 in (0, R - 2):
+        sl = slice(r0, r0 + 2)
+        ref = oracle.run(J, [1.2], 0.15, 0.15, 2, seed=2, s0=s0[sl], want_phi=True, r_first=r0)
+        scale = phi_scale(J, s0[sl], None, 0.15, 2, 0, r_first=r0)
+        assert (np.abs(out["phi"][sl] - ref["phi"]) / scale).max() <= TOL["bf16"]
+    del J
+    J = _hashed_pm1(n + 128, 8)
+    g = Gpu(J, precision="bf16")
+    with pytest.raises(nmfa.NmfaError) as ei:
+        g.run([1.2], 0.15, 0.15, R, seed=2, want_energy=False)
+    assert ei.value.code == nmfa.NMFA_EUNSUPPORTED
+    g.close()
+
+
 def test_full_c2_run_readout_and_energy():
     # The benchmark configuration end to end: SK N = 2000, 1024 replicas, t_f = 1000.
     n, R = 2000, 1024
