@@ -159,6 +159,29 @@ def test_zero_state_and_state_bound(prec):
     g.close()
 
 
+@pytest.mark.parametrize("prec", DENSE + ["csr_fp32"])
+def test_isolated_spins_single_step(prec):
+    # Spins with no coupling and no field (d_i = 0): their normalised field reads as
+    # 0 and Phi_i = sigma z (the limit of a vanishing field); the others are unaffected.
+    J = np.pad(inst.moebius(64), ((0, 3), (0, 3)))  # spins 64..66 isolated
+    n, R = J.shape[0], 40
+    s0 = _rand_state(R, n, 28)
+    if prec == "csr_fp32":
+        csr = inst.to_csr(J)
+        g, tol = Gpu(None, precision="fp32", csr=csr, n=n), TOL["fp32"]
+        ref = oracle.run(None, [0.9], 0.15, 0.15, R, seed=5, s0=s0, want_phi=True, csr=csr)
+    else:
+        g, tol = Gpu(J, precision=prec), TOL[prec]
+        ref = oracle.run(J, [0.9], 0.15, 0.15, R, seed=5, s0=s0, want_phi=True)
+    out = g.run([0.9], 0.15, 0.15, R, seed=5, s0=s0, want_phi=True)
+    g.close()
+    scale = phi_scale(J, s0, None, 0.15, 5, 0)
+    assert (np.abs(out["phi"] - ref["phi"]) / scale).max() <= tol
+    z = np.array([[oracle.gauss(5, 0, r, 0, i) for i in (64, 65, 66)] for r in range(R)])
+    np.testing.assert_allclose(ref["phi"][:, 64:], 0.15 * z, rtol=1e-15, atol=0)
+    assert np.all(np.isfinite(out["phi"]))
+
+
 # ---------------------------------------------------------------- sparse path
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_csr_single_step(prec):
