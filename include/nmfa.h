@@ -203,6 +203,12 @@ typedef struct nmfa_batch nmfa_batch;
 #define NMFA_BATCH_GRAPH 1    /* capture the batch's launches in a CUDA graph at creation */
 #define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128) per job by timing */
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
+/* Test only: leave the first group's last row-block tile out of the plan.  Nothing
+ * then publishes that tile's state, so the group's other tiles wait for a flag that
+ * is never set: their bounded waits give up (after 20 s for the first step),
+ * nmfa_batch_sync returns NMFA_ETIMEOUT, and the device stays usable.  The failure
+ * path is exercised without a GPU fault.  Needs a first job of more than 128 spins. */
+#define NMFA_BATCH_DEBUG_WITHHOLD_TILE 8
 
 /* Plans the batch (tiles of 128 spins x 64 or 128 replicas; the tile pipelines of
  * one replica block are co-scheduled on the persistent grid by list scheduling),

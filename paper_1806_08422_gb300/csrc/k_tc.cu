@@ -855,7 +855,8 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
   return NMFA_OK;
 }
 
-int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan) {
+int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,
+                  bool withhold_tile) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
   int ctas = 0;
   int rc = co_resident_ctas(jobs[0].bn, &ctas);
@@ -944,7 +945,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     double start = 0.0;
     for (int b = 0; b < nb; ++b) start = std::max(start, free_at[slots[b]]);
     for (int b = 0; b < nb; ++b) {
-      per_slot[slots[b]].push_back(TcItem{gi, b});
+      if (!(withhold_tile && gi == 0 && b == nb - 1)) per_slot[slots[b]].push_back(TcItem{gi, b});
       free_at[slots[b]] = start + gl[gi].dur;
     }
   }

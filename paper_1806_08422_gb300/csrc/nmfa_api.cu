@@ -1100,8 +1100,10 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     b->ws.emplace_back();
     if ((rc = ensure_buf(b->ws.back(), static_cast<size_t>(bytes)))) return fail(rc);
     b->plans.emplace_back();
+    const bool withhold = (options & NMFA_BATCH_DEBUG_WITHHOLD_TILE) && b->plans.size() == 1;  // the first plan
+    if (withhold && part[0].pb.n_pad <= 128) return fail(set_error(NMFA_EINVAL, "withheld tile needs n > 128"));
     if ((rc = tc_build_plan(part.data(), static_cast<int32_t>(part.size()), b->ws.back().p, bytes, b->status,
-                            &b->plans.back())))
+                            &b->plans.back(), withhold)))
       return fail(rc);
     // upload the plan once (kernel-parameter copies on the batch's stream)
     if ((rc = tc_upload_plan(b->plans.back(), b->own))) return fail(rc);

@@ -158,7 +158,9 @@ struct TcPlan {
 // Default replicas per tile (64 or 128) of a run of `replicas` replicas of an n_pad problem.
 int tc_pick_bn(int32_t replicas, int32_t n_pad);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
-int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan);
+// withhold_tile (test only): leave group 0's last row-block tile out of the work lists.
+int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,
+                  bool withhold_tile = false);
 int tc_upload_plan(const TcPlan& plan, cudaStream_t st);
 int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st);
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,

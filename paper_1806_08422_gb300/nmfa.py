@@ -224,6 +224,7 @@ class nmfa_job(ctypes.Structure):
 NMFA_BATCH_GRAPH = 1
 NMFA_BATCH_AUTOTUNE = 2
 NMFA_BATCH_BN64 = 4
+NMFA_BATCH_DEBUG_WITHHOLD_TILE = 8
 
 
 def make_job(T_dev, sigma, alpha, replicas, seed=0, stream_id=0, signs=None, energy=None, energy_i64=None):

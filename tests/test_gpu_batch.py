@@ -151,3 +151,31 @@ def test_mixed_precision_and_width_batch():
     nmfa.nmfa_batch_destroy(b)
     for p in problems:
         p.close()
+
+
+def test_withheld_tile_times_out_and_the_device_recovers():
+    # Failure detection without a GPU fault: one row-block tile of a group is left
+    # out of the plan, so its peers wait for an epoch flag that nothing sets.  Their
+    # bounded waits give up, the launch reports NMFA_ETIMEOUT, and the next launch
+    # on the same device gives the same results as before.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(300, 41)
+    p = nmfa.Problem(J, precision="bf16")
+    T_dev = torch.as_tensor(inst.schedule(20), device=dev)
+    ref_s, ref_e = _alone(p, T_dev, 96, 3, 1)
+    b, _ = _batch([p], [(T_dev, 96, 3, 1)], nmfa.NMFA_BATCH_DEBUG_WITHHOLD_TILE)
+    nmfa.nmfa_batch_launch(b)
+    with pytest.raises(nmfa.NmfaError) as ei:
+        nmfa.nmfa_batch_sync(b)
+    assert ei.value.code == nmfa.NMFA_ETIMEOUT
+    nmfa.nmfa_batch_destroy(b)
+    s, e = _alone(p, T_dev, 96, 3, 1)
+    np.testing.assert_array_equal(s, ref_s)
+    np.testing.assert_array_equal(e, ref_e)
+    b, outs = _batch([p], [(T_dev, 96, 3, 1)], 0)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    np.testing.assert_array_equal(outs[0][0].cpu().numpy(), ref_s)
+    nmfa.nmfa_batch_destroy(b)
+    p.close()
