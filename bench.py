@@ -206,7 +206,9 @@ def main():
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        from paper_1806_08422_gb300 import multi as _multi
+        _multi.init_ranks("nccl", timeout_s=300, device_id=torch.device("cuda", local))
     if rank == 0 or not os.path.exists(nmfa.LIB_PATH):
         __graft_entry__.build()
     if ws > 1:

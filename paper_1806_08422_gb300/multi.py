@@ -11,6 +11,24 @@ backends of torch.distributed.
 from __future__ import annotations
 
 
+def init_ranks(backend: str, timeout_s: float = 120.0, device_id=None, rank=None, world_size=None):
+    """torch.distributed.init_process_group with a finite timeout: a rank that never
+    joins, or that dies between steps, ends the other ranks' rendezvous or next
+    collective with an error after `timeout_s` instead of a hang.  Rank and world
+    size come from the environment (torchrun) unless given."""
+    import datetime
+
+    import torch.distributed as dist
+
+    kw = {"timeout": datetime.timedelta(seconds=float(timeout_s))}
+    if device_id is not None:
+        kw["device_id"] = device_id
+    if rank is not None:
+        kw["rank"] = int(rank)
+        kw["world_size"] = int(world_size)
+    dist.init_process_group(backend, **kw)
+
+
 def rank_stream(rank: int, base_stream: int = 0) -> int:
     """Noise stream id of rank `rank`'s replica batch."""
     return base_stream + rank

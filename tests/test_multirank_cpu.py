@@ -1,7 +1,9 @@
 """The multi-GPU (replicas-only) path's host logic on two gloo ranks on the CPU:
 each rank anneals its own batch on its own noise stream (here with the oracle, as
 no GPU is needed to check the bookkeeping), rank 0 gathers every rank's energies,
-and the whole-job time is the maximum over ranks."""
+and the whole-job time is the maximum over ranks.  Failure detection: a rank that
+never joins, or dies after joining, ends rank 0's rendezvous or collective with an
+error within the process group's timeout instead of a hang."""
 import os
 import socket
 
@@ -49,3 +51,49 @@ def test_two_rank_gather_and_timing(tmp_path):
         ref = oracle.run(J, inst.schedule(60), 0.15, 0.15, 8, seed=5, stream=10 + rank)["energy_i64"]
         np.testing.assert_array_equal(got[rank], ref)
     assert float(open(out + ".t").read()) == 2.0
+
+
+def _failing_worker(rank, world, port, mode, out_path):
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    if rank == 1 and mode == "never_joins":
+        os._exit(3)
+    stage = "init"
+    try:
+        multi.init_ranks("gloo", timeout_s=5, rank=rank, world_size=world)
+        if rank == 1:
+            os._exit(4)  # dies between steps, with nothing of its own in flight
+        stage = "gather"
+        multi.gather_to_rank0(torch.zeros(4, dtype=torch.int64))
+        stage = "completed"
+    except Exception as e:  # the failure reaches rank 0 as an error
+        stage = stage + " failed: " + type(e).__name__
+    with open(out_path, "w") as f:
+        f.write(stage)
+
+
+@pytest.mark.parametrize("mode", ["never_joins", "dies_after_join"])
+def test_failed_rank_is_detected_without_a_hang(tmp_path, mode):
+    import multiprocessing
+    import time
+
+    out = str(tmp_path / "rank0.txt")
+    ctx = multiprocessing.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, mode, out)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    procs[0].join(timeout=120)
+    alive = procs[0].is_alive()
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+        p.join()
+    assert not alive, "rank 0 hung"
+    assert procs[0].exitcode == 0
+    got = open(out).read()
+    assert ("init failed" if mode == "never_joins" else "gather failed") in got, got
+    assert time.time() - t0 < 120
