@@ -102,19 +102,30 @@ def _dist():
     return ws, rank, local
 
 
+def sources_digest(paths):
+    """SHA-256 of the kernel sources' code: `//` comments, trailing blanks and empty
+    lines are left out, so that editing a comment does not invalidate a capture."""
+    import hashlib
+    import re
+
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            for line in f:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the tensor kernel from the committed ncu capture of the
-    bench workload, or None when the kernel sources have changed since the capture."""
-    import hashlib
-
+    bench workload, or None when the kernel sources' code has changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "nmfa_tc_kernel_sk2000_r1024_traffic.json")) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        for p in rec["sources"]:
-            with open(os.path.join(ROOT, p), "rb") as f:
-                h.update(f.read())
-        return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+        ok = sources_digest(rec["sources"]) == rec["sources_code_sha256"]
+        return rec["dram_bytes_per_launch"] if ok else None
     except Exception:
         return None
 

@@ -11,8 +11,10 @@
 // work list the host planned for it:
 //   - the TMA warp streams 128-deep K slices of J's row block and of S's replica
 //     block into a ring of shared-memory slots (128-byte swizzle); the J slices of
-//     a step start before the step's state is published, the S slices after the
-//     whole warp has seen every row block's epoch flag of the group reach the step;
+//     a step start before the step's state is published, the tile's own S slice
+//     (the first of its sweep) as soon as its own epoch flag reaches the step, and
+//     the other S slices after the whole warp has seen every row block's epoch flag
+//     of the group reach the step;
 //   - the MMA warp issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of
 //     the converged warp) into one of two TMEM accumulators, releasing ring slots
 //     and the accumulator with tcgen05.commit;
@@ -31,7 +33,8 @@
 // state; for integer problems one more product of J with the sign vectors gives the
 // Eq. (1) energies exactly.
 //
-// Every wait (mbarrier or flag) is bounded by a 2-second wall-clock limit; on
+// Every wait (mbarrier or flag) is bounded by a 2-second wall-clock limit (20 s for
+// the first flag wait of a group, which may follow groups scheduled before it); on
 // expiry the pipeline records NMFA's timeout status, drains its own TMA copies and
 // MMAs, and the CTA frees its TMEM and returns.
 #include <cuda.h>
