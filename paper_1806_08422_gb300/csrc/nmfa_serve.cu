@@ -103,8 +103,9 @@ int64_t request_footprint(const Request* r) {
   return jq + n * n + creation + scratch + io;
 }
 
-// Freeing device memory synchronises with the device, so finished requests are
-// handed to the reaper thread and the scheduler never blocks on it.
+// Finished requests are handed to the reaper thread, which destroys their problems
+// (nmfa_destroy waits for the problem's runs) and returns their buffers to the
+// memory pool, so that the scheduler never blocks on a release.
 void release(nmfa_server* s, Request* r) {
   std::lock_guard<std::mutex> g(s->mu);
   s->graveyard.push_back(r);
