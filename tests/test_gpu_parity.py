@@ -43,6 +43,21 @@ def test_single_step_phi(prec, n, R):
     g.close()
 
 
+@pytest.mark.parametrize("n,R", [(300, 200), (1000, 64)])
+def test_single_step_phi_bf16_real_field(n, R):
+    # The tensor path with a real-valued field h (kept in binary32 and folded into the
+    # accumulator as h_i + sigma z d_i): within the BF16 tolerance of the oracle.
+    J = inst.gnp_maxcut(n, 0.5, 200 + n)
+    h = inst.random_fields(n, 0.8, 201)
+    s0 = _rand_state(R, n, 202)
+    ref = oracle.run(J, [0.6], 0.15, 0.15, R, seed=77, stream=5, h=h, s0=s0, want_phi=True)
+    g = Gpu(J, h=h, precision="bf16")
+    out = g.run([0.6], 0.15, 0.15, R, seed=77, stream_id=5, s0=s0, want_phi=True)
+    g.close()
+    scale = phi_scale(J, s0, h, 0.15, 77, 5)
+    assert (np.abs(out["phi"] - ref["phi"]) / scale).max() <= TOL["bf16"]
+
+
 @pytest.mark.parametrize("prec", DENSE)
 def test_single_step_full_size_sampled(prec):
     # SK N = 2000 with 1024 replicas in the launch configuration of the benchmark;
