@@ -107,6 +107,27 @@ def test_sigma0_fp64_trajectory():
     g.close()
 
 
+@pytest.mark.parametrize("case", ["alpha1", "cold"])
+def test_special_case_trajectories_fp64(case):
+    # Algorithm 1's special cases on the GPU: alpha = 1 (synchronous deterministic
+    # mean-field annealing, no memory of the previous state) and a schedule so cold
+    # that tanh saturates (zero-temperature sign dynamics); sigma = 0, FP64.
+    n, R = 90, 4
+    J = inst.sk(n, 31)
+    h = inst.random_fields(n, 0.2, 32)
+    s0 = _rand_state(R, n, 33) * 0.2
+    if case == "alpha1":
+        T, alpha = inst.schedule(300), 1.0
+    else:
+        T, alpha = [1e-6] * 40, 0.5
+    ref = oracle.run(J, T, 0.0, alpha, R, h=h, s0=s0, want_state=True)
+    g = Gpu(J, h=h, precision="fp64")
+    out = g.run(T, 0.0, alpha, R, s0=s0, want_state=True)
+    g.close()
+    assert np.abs(out["state"] - ref["state"]).max() <= 1e-9
+    np.testing.assert_array_equal(out["signs"], ref["signs"])
+
+
 def test_sigma0_fp64_trajectory_from_state():
     n, R, t_f = 160, 6, 400
     J = inst.gnp_maxcut(n, 0.5, 4)
