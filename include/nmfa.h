@@ -62,10 +62,13 @@ typedef enum {
 typedef struct nmfa_problem nmfa_problem; /* opaque; owns device copies of (h, J) */
 
 /*
- * nmfa_create -- upload a dense Ising problem (Eq. (1)) and precompute, on the GPU in
- * FP64, the row norms d_i = sqrt(h_i^2 + sum_j J_ij^2) of Algorithm 1's field
- * (Sec. II: the root mean square of the terms acting on spin i).  A spin with
- * d_i = 0 gets a normalised field of 0.
+ * nmfa_create -- upload a dense Ising problem (Eq. (1)) and precompute in FP64 the
+ * row norms d_i = sqrt(h_i^2 + sum_j J_ij^2) of Algorithm 1's field (Sec. II: the
+ * root mean square of the terms acting on spin i), kept on the GPU: a kernel forms
+ * them from the FP64 couplings, or, for integer tensor-path problems, creation forms
+ * them on the host, where every term and the sum are exact integers and the square
+ * root is correctly rounded (the same values).  A spin with d_i = 0 gets a
+ * normalised field of 0.
  *   n         number of spins, 1 <= n <= 65536 (the CUDA-core paths accept less;
  *             NMFA_EUNSUPPORTED when the state does not fit on chip)
  *   h         host, n float64, or NULL for h = 0
@@ -142,9 +145,9 @@ int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
  * The tensor kernel's scratch (two BF16 copies of the state and one epoch flag per
  * tile) comes from a static device array of 16 MiB that every GPU loading this
  * library holds until the process exits.  The scratch needed is
- * 4 * ceil(R/BN)*BN * ceil(n/128)*128 bytes plus the flags (BN = 64 for R <= 64,
- * else 128); larger sizes return NMFA_EINVAL with nothing launched (e.g. n = 2000
- * takes up to R = 1920).  The flags are cleared on the stream before each launch;
+ * 4 * ceil(R/BN)*BN * ceil(n/128)*128 bytes plus the flags (BN, the run's tile
+ * width, is 64 for R <= 64 and for small problems, else 128); larger sizes return
+ * NMFA_EINVAL with nothing launched (e.g. n = 2000 takes up to R = 1920).  The flags are cleared on the stream before each launch;
  * the state buffers are fully written by the kernel before they are read.
  *   signs_dev  R*n int8, required (no scratch is made for signs)
  *   energy_dev, energy_i64_dev  as in nmfa_run_device (may be NULL)
@@ -205,7 +208,7 @@ typedef struct nmfa_batch nmfa_batch;
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
 /* Test only: leave the first group's last row-block tile out of the plan.  Nothing
  * then publishes that tile's state, so the group's other tiles wait for a flag that
- * is never set: their bounded waits give up (after 20 s for the first step),
+ * is never set: their bounded waits give up (within 2 s, 20 s at most),
  * nmfa_batch_sync returns NMFA_ETIMEOUT, and the device stays usable.  The failure
  * path is exercised without a GPU fault.  Needs a first job of more than 128 spins. */
 #define NMFA_BATCH_DEBUG_WITHHOLD_TILE 8
