@@ -204,8 +204,9 @@ typedef struct {
 typedef struct nmfa_batch nmfa_batch;
 
 #define NMFA_BATCH_GRAPH 1    /* capture the batch's launches in a CUDA graph at creation */
-#define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128) per job by timing */
+#define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128/256) per job by timing */
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
+#define NMFA_BATCH_BN128 16   /* force 128 replicas per tile (results do not change) */
 /* Test only: leave the first group's last row-block tile out of the plan.  Nothing
  * then publishes that tile's state, so the group's other tiles wait for a flag that
  * is never set: their bounded waits give up (within 2 s, 20 s at most),
@@ -213,7 +214,7 @@ typedef struct nmfa_batch nmfa_batch;
  * path is exercised without a GPU fault.  Needs a first job of more than 128 spins. */
 #define NMFA_BATCH_DEBUG_WITHHOLD_TILE 8
 
-/* Plans the batch (tiles of 128 spins x 64 or 128 replicas; the tile pipelines of
+/* Plans the batch (tiles of 128 spins x 64, 128 or 256 replicas; the tile pipelines of
  * one replica block are co-scheduled on the persistent grid by list scheduling),
  * allocates its workspace, uploads the plan and, with NMFA_BATCH_GRAPH, captures the
  * launch sequence as a CUDA graph.  Nothing runs until nmfa_batch_launch.  The
@@ -230,7 +231,7 @@ int nmfa_batch_sync(nmfa_batch* b);
 int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes);
 void nmfa_batch_destroy(nmfa_batch* b);
 
-/* Autotuner entry: the replicas-per-tile (64 or 128) the tensor path would use for
+/* Autotuner entry: the replicas-per-tile (64, 128 or 256) the tensor path would use for
  * `replicas` replicas of this problem, measured once per (n rounded to 128,
  * replicas) and cached for the process. */
 int nmfa_autotune_bn(nmfa_problem* p, int32_t replicas, int32_t* bn);

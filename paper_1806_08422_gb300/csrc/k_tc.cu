@@ -3,12 +3,12 @@
 // One persistent launch runs all t_f steps of Algorithm 1 for a batch of replicas
 // (one run, or a ragged batch of runs of different instances).  The coupling
 // product of the field update over all replicas is the GEMM P = J S (J: n x n,
-// S: n x R).  The replicas of a run are split into groups of BN (64 or 128); a
+// S: n x R).  The replicas of a run are split into groups of BN (64, 128 or 256); a
 // group's output is tiled by row blocks of 128 spins, and each (group, row block)
 // item is owned by one tile pipeline for the group's whole run.  A pipeline is a
-// TMA warp, an MMA warp and BN / 8 epilogue warps; a CTA holds one pipeline for
-// BN = 128 and two independent ones for BN = 64 (one CTA per SM), and walks the
-// work list the host planned for it:
+// TMA warp, an MMA warp and BN / 8 epilogue warps (16 for BN = 256); a CTA holds
+// one pipeline for BN = 128 or 256 and two independent ones for BN = 64 (one CTA per
+// SM), and walks the work list the host planned for it:
 //   - the TMA warp streams 128-deep K slices of J's row block and of S's replica
 //     block into a ring of shared-memory slots (128-byte swizzle); the J slices of
 //     a step start before the step's state is published, the tile's own S slice
@@ -68,7 +68,7 @@ constexpr int kAtoms = 2;
 constexpr int kKSlot = kAtoms * kBK;
 constexpr int kMaxStages = 3;
 constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
-// Geometry per tile width BN (replicas per tile, the MMA's N: 64 or 128).
+// Geometry per tile width BN (replicas per tile, the MMA's N: 64, 128 or 256).
 //   Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
 //   tile takes BN / 8 of them (16 for 128-replica tiles, 8 for 64).
 //   One CTA per SM: a kernel that allocates TMEM is given one CTA per SM by the
@@ -80,23 +80,32 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   MMAs fill the time the first spends in its epilogue and state exchange.
 //   TMEM columns of a pipeline (from its base): accumulators [0, BN) and
 //   [BN, 2 BN) (step g uses g % 2), FP32 master state [2 BN, 3 BN).
+//   A 256-replica CTA (for runs whose 128-replica tiles would need more than one
+//   wave of the grid) has one pipeline of 16 epilogue warps with 64 columns each, a
+//   ring of 2 slots of 96 KB, and a single accumulator [0, 256) beside the master
+//   state [256, 512): its MMAs (N = 256) run near the full tensor rate, and each
+//   step's bias is written into the accumulator after the update has read it.
 template <int BN>
 struct TcShape {
-  static constexpr int kEpiWarps = BN / 8;
+  static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
+  static constexpr int kColsPerWarp = BN == 256 ? 64 : 32;
+  static constexpr int kEpiWarps = BN == 256 ? 16 : BN / 8;
   static constexpr int kSubs = BN == 64 ? 2 : 1;   // tile pipelines per CTA
   static constexpr int kSubWarps = 2 + kEpiWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
-  static constexpr int kStages = BN == 64 ? 2 : 3;  // ring slots per pipeline
+  static constexpr int kStages = BN == 128 ? 3 : 2;  // ring slots per pipeline
   static constexpr uint32_t kBAtomBytes = BN * 128;  // one B (S) atom: BN rows x 128 bytes
   static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
   static constexpr uint32_t kRingBytes = kStages * kStageBytes;
   static constexpr size_t kSmemBytes = static_cast<size_t>(kSubs) * kRingBytes + 1024;
   static constexpr uint32_t kTmemCols = 512;  // allocated once per CTA
   static constexpr uint32_t kSubCols = kTmemCols / kSubs;
-  static constexpr uint32_t kColAcc1 = BN;
-  static constexpr uint32_t kColMaster = 2 * BN;
+  static constexpr uint32_t kColAcc1 = kDoubleAcc ? BN : 0;
+  static constexpr uint32_t kColMaster = kDoubleAcc ? 2 * BN : BN;
   static_assert(kStages <= kMaxStages, "ring slots");
-  static_assert(3 * BN <= kSubCols, "TMEM columns");
+  static_assert(kColMaster + BN <= kSubCols, "TMEM columns");
+  static_assert(kEpiWarps * kColsPerWarp == 4 * BN, "every (quarter, column) pair once");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 constexpr int kMaxSubs = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -201,9 +210,16 @@ __device__ __forceinline__ void acquire_tensormap(const void* m) {
                : "memory");
 }
 
+// Barrier that tells the MMA issuer step g's bias is in place: one per accumulator.
+template <int BN>
+__device__ __forceinline__ uint32_t bias_bar(SharedCtl* ctl, uint32_t g) {
+  return ptx::smem_u32(&ctl->bias_ready[TcShape<BN>::kDoubleAcc ? (g & 1u) : 0u]);
+}
+
 // (A) the bias of one step, h_i + sigma z d_i, written into the accumulator the step
-// will use (the Gaussian draws do not depend on the state, so this runs while the
-// tensor core still computes the previous step), then signalled to the MMA issuer.
+// will use (the Gaussian draws do not depend on the state, so with two accumulators
+// this runs while the tensor core still computes the previous step), then signalled
+// to the MMA issuer.
 template <int BN>
 __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base, int col0, int rbase, int i,
                                            uint32_t stream, const RoundKeys& rk, float sigma_ns, float dd, float hi,
@@ -211,7 +227,7 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
   const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll 1
-  for (int cc = 0; cc < kColsPerWarp; cc += 16) {
+  for (int cc = 0; cc < TcShape<BN>::kColsPerWarp; cc += 16) {
 #pragma unroll
     for (int gq = 0; gq < 4; ++gq) {
       const int r4 = rbase + cc + 4 * gq;
@@ -227,7 +243,7 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
-  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready[g & 1u]));
+  if (lane == 0) ptx::mbar_arrive(bias_bar<BN>(ctl, g));
 }
 
 // (A') the accumulator start of the energy product: 2 h_i, no noise.
@@ -239,11 +255,11 @@ __device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __float_as_uint(2.0f * hi);
 #pragma unroll 1
-  for (int cc = 0; cc < kColsPerWarp; cc += 16) ptx::tmem_st16(acc + col0 + cc, v);
+  for (int cc = 0; cc < TcShape<BN>::kColsPerWarp; cc += 16) ptx::tmem_st16(acc + col0 + cc, v);
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
-  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&ctl->bias_ready[g & 1u]));
+  if (lane == 0) ptx::mbar_arrive(bias_bar<BN>(ctl, g));
 }
 
 // (C) Energy readout (Eq. 1) of one warp's 32 spins x 32 replicas.  The accumulator
@@ -308,7 +324,8 @@ __device__ __noinline__ void energy_readout(const TcGroup* __restrict__ g, uint3
 template <int BN, int QOFF>
 __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
                                               SharedCtl* ctl, int32_t* status, uint32_t& gstep) {
-  constexpr int kCW = kColsPerWarp;
+  constexpr int kCW = TcShape<BN>::kColsPerWarp;
+  constexpr bool kDouble = TcShape<BN>::kDoubleAcc;
   constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1, kColMaster = TcShape<BN>::kColMaster;
   const int q = (e + QOFF) & 3;
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
@@ -368,10 +385,12 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     inv_T = __shfl_sync(0xffffffffu, inv_T, 0);
     __nv_bfloat16* Snext = S16 + static_cast<size_t>((t + 1) & 1) * plane;
     // the next step's bias goes into the other accumulator (read last two steps ago)
-    if (t + 1 < t_f)
-      write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
-    else if (energy_pass)
-      write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
+    if constexpr (kDouble) {
+      if (t + 1 < t_f)
+        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+      else if (energy_pass)
+        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
+    }
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
     ptx::tc_fence_after();
@@ -419,6 +438,14 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     ptx::fence_proxy_async_global();
     __syncwarp();
     if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
+    if constexpr (!kDouble) {
+      // one accumulator: the next step's bias goes in once this step's product has
+      // been read (the draws then overlap the other tiles' publication and the copies)
+      if (t + 1 < t_f)
+        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+      else if (energy_pass)
+        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
+    }
   }
   // sign readout of Algorithm 1: sign of the FP32 master state, zero reads as +1
   if (!__all_sync(0xffffffffu, !aborted(ctl))) return false;
@@ -442,8 +469,11 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   if (energy_pass) {
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
     ptx::tc_fence_after();
-    energy_readout(g, lane_base + ((gstep & 1u) ? kColAcc1 : 0u), lane_base + kColMaster, col0, rbase, valid, lane,
-                   static_cast<uint32_t>(n_pad / kBM) * static_cast<uint32_t>(BN / 8));
+    // 32 columns per call: parts = tiles x BN / 32 per group
+#pragma unroll 1
+    for (int c2 = 0; c2 < kCW; c2 += kColsPerWarp)
+      energy_readout(g, lane_base + ((gstep & 1u) ? kColAcc1 : 0u), lane_base + kColMaster, col0 + c2, rbase + c2,
+                     valid, lane, static_cast<uint32_t>(n_pad / kBM) * static_cast<uint32_t>(BN / 8));
     ++gstep;
   }
   return true;
@@ -614,8 +644,9 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       for (int t = 0; t < steps && ok; ++t, ++gstep) {
         // the epilogue has written this step's bias (h + sigma z d) into the
         // accumulator the step uses; the product accumulates onto it
-        ok = __all_sync(0xffffffffu,
-                        wait_bar(ptx::smem_u32(&ctl.bias_ready[gstep & 1u]), (gstep >> 1) & 1u, &ctl, status));
+        ok = __all_sync(0xffffffffu, wait_bar(bias_bar<BN>(&ctl, gstep),
+                                              TcShape<BN>::kDoubleAcc ? ((gstep >> 1) & 1u) : (gstep & 1u), &ctl,
+                                              status));
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
@@ -788,10 +819,11 @@ int co_resident_ctas_bn(int* capacity) {
   return NMFA_OK;
 }
 int co_resident_ctas(int bn, int* capacity) {
-  return bn == 64 ? co_resident_ctas_bn<64>(capacity) : co_resident_ctas_bn<128>(capacity);
+  return bn == 64 ? co_resident_ctas_bn<64>(capacity)
+                  : bn == 256 ? co_resident_ctas_bn<256>(capacity) : co_resident_ctas_bn<128>(capacity);
 }
 // Work-list slots (tile pipelines) of the co-resident grid.
-int tc_subs(int bn) { return bn == 64 ? TcShape<64>::kSubs : TcShape<128>::kSubs; }
+int tc_subs(int bn) { return bn == 64 ? TcShape<64>::kSubs : 1; }
 int co_resident_slots(int bn, int* slots) {
   int ctas = 0;
   const int rc = co_resident_ctas(bn, &ctas);
@@ -822,6 +854,14 @@ int tc_pick_bn(int32_t replicas, int32_t n_pad) {
   }
   const int64_t tiles128 = static_cast<int64_t>(n_pad / kBM) * ((replicas + 127) / 128);
   if (n_pad <= 1024 && sms > 0 && 2 * tiles128 <= sms) return 64;
+  // 256 replicas per tile when 128-replica tiles would need more than one wave of
+  // the grid (one CTA per SM) and a step has at least 16 K slices: half the tiles,
+  // each streaming J once for twice the replicas with MMAs of N = 256.  Their single
+  // accumulator puts the next step's noise draws after the update, which only a long
+  // enough product hides (200-step runs, ms, 256 against 128: n = 2048, R = 2048:
+  // 3.77 / 4.33; n = 4096, R = 1024: 6.04 / 6.90; n = 8192, R = 512: 11.7 / 13.9;
+  // but n = 1536, R = 4096: 6.57 / 5.32).
+  if (sms > 0 && tiles128 > sms && replicas > 128 && n_pad >= 2048) return 256;
   return 128;
 }
 
@@ -1006,8 +1046,13 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
     return rc;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.grid, 1, 1);
-  cfg.blockDim = dim3(plan.bn == 64 ? TcShape<64>::kThreads : TcShape<128>::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = plan.bn == 64 ? TcShape<64>::kSmemBytes : TcShape<128>::kSmemBytes;
+  cfg.blockDim = dim3(plan.bn == 64    ? TcShape<64>::kThreads
+                      : plan.bn == 256 ? TcShape<256>::kThreads
+                                       : TcShape<128>::kThreads,
+                      1, 1);
+  cfg.dynamicSmemBytes = plan.bn == 64    ? TcShape<64>::kSmemBytes
+                         : plan.bn == 256 ? TcShape<256>::kSmemBytes
+                                          : TcShape<128>::kSmemBytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -1018,8 +1063,9 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   const TcGroup* dg = reinterpret_cast<const TcGroup*>(d + plan.groups_off);
   const TcItem* di = reinterpret_cast<const TcItem*>(d + plan.items_off);
   const int32_t* df = reinterpret_cast<const int32_t*>(d + plan.first_off);
-  const cudaError_t ce = plan.bn == 64 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
-                                       : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128>, dg, di, df, plan.status);
+  const cudaError_t ce = plan.bn == 64    ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
+                         : plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256>, dg, di, df, plan.status)
+                                          : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128>, dg, di, df, plan.status);
   if ((rc = cuda_error(ce, "tensor kernel launch"))) return rc;
   count_launch();
   return NMFA_OK;

@@ -1086,11 +1086,12 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.rp.energy_i64 = jb.energy_i64_dev;
     b->energy_fused.push_back(tc_fuses_energy(t.pb, t.rp) ? 1 : 0);
     t.bn = (options & NMFA_BATCH_BN64) ? 64
+           : (options & NMFA_BATCH_BN128) ? 128
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
                                              : tc_pick_bn(jb.replicas, p->n_pad);
     b->bn.push_back(t.bn);
   }
-  for (int bnv : {128, 64}) {
+  for (int bnv : {256, 128, 64}) {
     std::vector<TcJob> part;
     for (const TcJob& t : tj)
       if (t.bn == bnv) part.push_back(t);
@@ -1188,7 +1189,7 @@ int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Autotuner: replicas per tile (bn = 64 or 128) for the tensor path, chosen by
+// Autotuner: replicas per tile (bn = 64, 128 or 256) for the tensor path, chosen by
 // timing a short run of each candidate on the problem itself and cached by the
 // run's shape (n_pad, replicas) only, so that an instance's tiling (and hence
 // its results) never depends on what else shares a batch.  Results are identical
@@ -1222,7 +1223,8 @@ static int nmfa_autotuned_bn(nmfa_problem* p, int32_t replicas) {
     std::vector<double> Th(t_f, 1.0);
     okc = cudaMemcpy(T, Th.data(), sizeof(double) * t_f, cudaMemcpyHostToDevice) == cudaSuccess;
   }
-  for (int bn : {64, 128}) {
+  for (int bn : {64, 128, 256}) {
+    if (bn == 256 && replicas <= 128) continue;
     if (!okc) break;
     TcJob jb{};
     jb.pb.n = p->n;

@@ -144,7 +144,7 @@ int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes);
 struct TcJob {
   TcProblem pb;
   RunParams rp;
-  int bn;                  // replicas per tile: 64 or 128
+  int bn;                  // replicas per tile: 64, 128 or 256
 };
 struct TcPlan {
   std::vector<unsigned char> host;   // group descriptors, items, per-CTA offsets
@@ -155,7 +155,7 @@ struct TcPlan {
   int32_t* status = nullptr;
   double makespan = 0.0;             // scheduler's estimate (relative units)
 };
-// Default replicas per tile (64 or 128) of a run of `replicas` replicas of an n_pad problem.
+// Default replicas per tile (64, 128 or 256) of a run of `replicas` replicas of an n_pad problem.
 int tc_pick_bn(int32_t replicas, int32_t n_pad);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
 // withhold_tile (test only): leave group 0's last row-block tile out of the work lists.

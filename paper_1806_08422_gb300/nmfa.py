@@ -224,6 +224,7 @@ class nmfa_job(ctypes.Structure):
 NMFA_BATCH_GRAPH = 1
 NMFA_BATCH_AUTOTUNE = 2
 NMFA_BATCH_BN64 = 4
+NMFA_BATCH_BN128 = 16
 NMFA_BATCH_DEBUG_WITHHOLD_TILE = 8
 
 

@@ -179,3 +179,33 @@ def test_withheld_tile_times_out_and_the_device_recovers():
     np.testing.assert_array_equal(outs[0][0].cpu().numpy(), ref_s)
     nmfa.nmfa_batch_destroy(b)
     p.close()
+
+
+def test_256_replica_tiles_match_64_replica_tiles():
+    # A run whose 128-replica tiles would need two waves takes 256-replica tiles
+    # (one accumulator, bias written after the update); its signs and Eq. (1)
+    # energies are bit-identical to the same run on 64-replica tiles.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    n, R = 2048, 2048
+    J = inst.sk(n, 52)
+    p = nmfa.Problem(J, precision="bf16")
+    T_dev = torch.as_tensor(inst.schedule(25), device=dev)
+    b, outs = _batch([p], [(T_dev, R, 6, 2)], 0)
+    assert nmfa.nmfa_batch_info(b)["groups"] == R // 256
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    s256, e256 = outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy()
+    nmfa.nmfa_batch_destroy(b)
+    b, outs = _batch([p], [(T_dev, R, 6, 2)], nmfa.NMFA_BATCH_BN64)
+    assert nmfa.nmfa_batch_info(b)["groups"] == R // 64
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    np.testing.assert_array_equal(outs[0][0].cpu().numpy(), s256)
+    np.testing.assert_array_equal(outs[0][1].cpu().numpy(), e256)
+    nmfa.nmfa_batch_destroy(b)
+    s, e = _alone(p, T_dev, R, 6, 2)
+    np.testing.assert_array_equal(s, s256)
+    for r in (0, 777, R - 1):
+        assert e256[r] == oracle.energy_i64(J, s256[r])
+    p.close()

@@ -58,6 +58,23 @@ def test_single_step_phi_bf16_real_field(n, R):
     assert (np.abs(out["phi"] - ref["phi"]) / scale).max() <= TOL["bf16"]
 
 
+def test_single_step_256_replica_tiles():
+    # n = 2048 with 2048 replicas: 128-replica tiles would need two waves of the
+    # grid, so the run takes 256-replica tiles (N = 256 MMAs, one accumulator);
+    # sampled replica slices of every tile position against the oracle.
+    n, R = 2048, 2048
+    J = inst.sk(n, 61)
+    s0 = _rand_state(R, n, 62)
+    g = Gpu(J, precision="bf16")
+    out = g.run([1.1], 0.15, 0.15, R, seed=3, stream_id=4, s0=s0, want_phi=True)
+    g.close()
+    for r0 in (0, 250, 1020, R - 5):
+        sl = slice(r0, r0 + 5)
+        ref = oracle.run(J, [1.1], 0.15, 0.15, 5, seed=3, stream=4, s0=s0[sl], want_phi=True, r_first=r0)
+        scale = phi_scale(J, s0[sl], None, 0.15, 3, 4, r_first=r0)
+        assert (np.abs(out["phi"][sl] - ref["phi"]) / scale).max() <= TOL["bf16"], r0
+
+
 @pytest.mark.parametrize("prec", DENSE)
 def test_single_step_full_size_sampled(prec):
     # SK N = 2000 with 1024 replicas in the launch configuration of the benchmark;
