@@ -64,18 +64,25 @@ __device__ __forceinline__ void draw(NoiseKey key, uint32_t stream, int r0, int 
   for (int g = 0; g < G; ++g) {
     const uint4 w = noise_words(key, stream, static_cast<uint32_t>((r0 >> 2) + g),
                                 static_cast<uint32_t>(t), static_cast<uint32_t>(i));
-    if constexpr (sizeof(T) == 4 && RC < 4) {
+    if constexpr (RC < 4) {
       // fewer than four replicas per thread: only the Box-Muller pair(s) of the
-      // words this thread's replicas use (replica 4p + c takes word c; pair c / 2)
+      // words this thread's replicas use (replica 4p + c takes word c; pair c / 2),
+      // each with the same operations as the four-draw helpers, so the values are
+      // theirs bit for bit
       const int off = r0 & 3;
 #pragma unroll
       for (int k = 0; k < RC; ++k) {
         const int c = off + k;
         if (k == 0 || (c & 1) == 0) {  // a pair not yet drawn
           const uint32_t wa = (c & 2) ? w.z : w.x, wb = (c & 2) ? w.w : w.y;
-          const float ra = sqrtf(-2.0f * logf(u01_f32(wa)));
-          float sb, cb;
-          sincospif(2.0f * u01_f32(wb), &sb, &cb);
+          T ra, sb, cb;
+          if constexpr (sizeof(T) == 4) {
+            ra = sqrtf(-2.0f * logf(u01_f32(wa)));
+            sincospif(2.0f * u01_f32(wb), &sb, &cb);
+          } else {
+            ra = sqrt(-2.0 * log(u01_f64(wa)));
+            sincospi(2.0 * u01_f64(wb), &sb, &cb);
+          }
           z[k] = (c & 1) ? ra * sb : ra * cb;
           if (k + 1 < RC && (c & 1) == 0) z[k + 1] = ra * sb;
         }
