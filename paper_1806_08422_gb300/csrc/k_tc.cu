@@ -11,10 +11,9 @@
 // SM), and walks the work list the host planned for it:
 //   - the TMA warp streams 128-deep K slices of J's row block and of S's replica
 //     block into a ring of shared-memory slots (128-byte swizzle); the J slices of
-//     a step start before the step's state is published, the tile's own S slice
-//     (the first of its sweep) as soon as its own epoch flag reaches the step, and
-//     the other S slices after the whole warp has seen every row block's epoch flag
-//     of the group reach the step;
+//     a step start before the step's state is published, and each S slice as soon
+//     as the epoch flag of the row block that wrote it reaches the step, in a fixed
+//     K order that starts with the tile's own slice;
 //   - the MMA warp issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of
 //     the converged warp) into one of two TMEM accumulators, releasing ring slots
 //     and the accumulator with tcgen05.commit;
@@ -34,7 +33,8 @@
 // Eq. (1) energies exactly.
 //
 // Every wait (mbarrier or flag) is bounded by a 2-second wall-clock limit (20 s for
-// the first flag wait of a group, which may follow groups scheduled before it); on
+// the flag waits of a group's first step, which may follow groups scheduled before
+// it); on
 // expiry the pipeline records NMFA's timeout status, drains its own TMA copies and
 // MMAs, and the CTA frees its TMEM and returns.
 #include <cuda.h>
@@ -183,13 +183,31 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SharedCt
 // Warp-wide wait until every row block's epoch counter of one group reaches
 // `need`: lane l polls row blocks l, l+32, ... in parallel.  Returns false (on every
 // lane) on abort/timeout.
-__device__ __forceinline__ bool wait_group_flags(const uint32_t* f0, int nb, uint32_t need, int lane,
-                                                 SharedCtl* ctl, int32_t* status, uint64_t limit_ns) {
+// Row blocks of a group seen published at the current step: lane l holds bit j for
+// row block l + 32 j (a group has at most 152 row blocks, so j < 5).
+__device__ __forceinline__ bool block_seen(uint32_t seen, int k) {
+  return (__shfl_sync(0xffffffffu, seen, k & 31) >> (k >> 5)) & 1u;
+}
+
+// Wait (bounded) until row block k of the group has published step counter `need`.
+// Each poll reads every counter not yet seen, one acquire load per row block, so one
+// round trip to L2 also finds the blocks the producer will need next.  The warp
+// barrier and the proxy fence after the poll order the owning lane's acquire before
+// the copies that the elected lane issues from that block's state.
+__device__ __forceinline__ bool wait_block(const uint32_t* f0, int nb, int k, uint32_t need, int lane,
+                                           uint32_t& seen, SharedCtl* ctl, int32_t* status, bool first_step) {
+  if (block_seen(seen, k)) return true;
+  const uint64_t limit_ns = first_step ? kStartTimeoutNs : kTimeoutNs;
   const uint64_t t0 = ptx::globaltimer_ns();
   while (true) {
-    bool mine = true;
-    for (int rb = lane; rb < nb; rb += 32) mine = mine && (ptx::ld_acquire_gpu(f0 + rb) >= need);
-    if (__all_sync(0xffffffffu, mine)) return true;
+    uint32_t bit = 1u;
+    for (int rb = lane; rb < nb; rb += 32, bit <<= 1)
+      if (!(seen & bit) && ptx::ld_acquire_gpu(f0 + rb) >= need) seen |= bit;
+    __syncwarp();
+    if (block_seen(seen, k)) {
+      ptx::fence_proxy_async_global();
+      return true;
+    }
     int stop = 0;
     if (lane == 0) {
       if (aborted(ctl)) {
@@ -502,10 +520,9 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
   if (lw == 0) {
     // ------------------------------------------------------------ TMA producer
     // Per step: claim the first ring slots and start their J slices at once (J
-    // does not depend on the previous step), wait with the whole warp until every
-    // row block of the group has published the step's state, then issue the S
-    // slices of the claimed slots and stream the rest of the step.  The whole warp
-    // runs the loop; one elected lane issues each copy.
+    // does not depend on the previous step), then issue each slot's S slice once its
+    // row block has published the step's state, and stream the rest of the step.
+    // The whole warp runs the loop; one elected lane issues each copy.
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
     uint32_t stage = 0, phase = 0;  // next ring slot to fill
     uint32_t filled = 0;            // ring slots whose copies were issued (for the drain)
@@ -551,38 +568,17 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           }
           if (++ks == KB) ks = 0;
         }
-        // The first claimed slot is the tile's own K slice: after the first step its S
-        // half is copied as soon as this tile has published, before the other row
-        // blocks have, so the step's first MMAs need not wait for the slowest tile.
-        const int early = (t > 0 && claimed > 0 && nb > 1) ? 1 : 0;
-        if (early) {  // (the copy is issued on abort too, so that the slot's barrier completes)
-          if (ok)
-            ok = wait_group_flags(gflags + b, 1, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
-                                  kTimeoutNs);
-          __syncwarp();
-          if (ok) ptx::fence_proxy_async_global();
-#pragma unroll
-          for (int a = 0; a < kAtoms; ++a)
-            ptx::tma_load_2d_warp(ring + claim_stage * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
-                                  kslice_base * kKSlot + a * kBK, sy, full0 + 8u * claim_stage);
-        }
-        if (ok)
-          ok = wait_group_flags(gflags, nb, static_cast<uint32_t>(kEpiWarps * (t + 1)), lane, &ctl, status,
-                                t == 0 ? kStartTimeoutNs : kTimeoutNs);
-        // each lane acquired its own row blocks' counters; the warp barrier orders
-        // those acquires before the elected lane's copies (memory ordering within the warp)
-        __syncwarp();
-        if (ok) ptx::fence_proxy_async_global();
-        // the S halves of the other claimed slots (also on abort, so that their
-        // barriers complete)
+        // Each S half is copied as soon as its own row block has published the step, in
+        // the fixed K order (so the FP32 sums keep one order): the tile's own slice
+        // first, right after this tile's epilogue, then the others, so that the MMAs on
+        // early blocks overlap the wait for a late one.
+        const uint32_t need = static_cast<uint32_t>(kEpiWarps * (t + 1));
+        uint32_t seen = 0;
         {
           uint32_t st = claim_stage;
           int ks2 = kslice_base;
-          if (early) {
-            if (++st == kStages) st = 0;
-            if (++ks2 == KB) ks2 = 0;
-          }
-          for (int kb = early; kb < claimed; ++kb) {
+          for (int kb = 0; kb < claimed; ++kb) {  // (issued on abort too, so that the barriers complete)
+            if (ok) ok = wait_block(gflags, nb, ks2, need, lane, seen, &ctl, status, t == 0);
 #pragma unroll
             for (int a = 0; a < kAtoms; ++a)
               ptx::tma_load_2d_warp(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
@@ -598,17 +594,20 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           const uint32_t sA = ring + stage * kStageBytes;
           ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
 #pragma unroll
-          for (int a = 0; a < kAtoms; ++a) {
+          for (int a = 0; a < kAtoms; ++a)
             ptx::tma_load_2d_warp(sA + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, full0 + 8u * stage);
+          ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
+#pragma unroll
+          for (int a = 0; a < kAtoms; ++a)
             ptx::tma_load_2d_warp(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy,
                                   full0 + 8u * stage);
-          }
           ++filled;
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
           if (++ks == KB) ks = 0;
+          if (!ok) break;
         }
       }
     }
