@@ -431,10 +431,18 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
         pa[k] = __float_as_uint(phi);
       }
       if (write_phi) {  // last step of a debug run only (warp-uniform branch)
+        if constexpr (BN == 64) {
+          double* po = phi_out + static_cast<int64_t>(rbase + cc) * n + i;
+          const int rmax = valid ? R - (rbase + cc) : 0;  // columns k < rmax are replicas of the run
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int r = rbase + cc + k;
-          if (valid && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(__uint_as_float(pa[k]));
+          for (int k = 0; k < 16; ++k)
+            if (k < rmax) po[k * n] = static_cast<double>(__uint_as_float(pa[k]));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int r = rbase + cc + k;
+            if (valid && r < R) phi_out[static_cast<int64_t>(r) * n + i] = static_cast<double>(__uint_as_float(pa[k]));
+          }
         }
       }
       ptx::tmem_st16(lane_base + kColMaster + col0 + cc, ms);
