@@ -151,6 +151,12 @@ struct SharedCtl {
   // uses of the same barrier each warp waits for acc_full of the step in between,
   // which implies the earlier phase completed.
   uint64_t bias_ready[2];
+  // Completes once per publication of this pipeline's tile state that the producer
+  // copies from (publications 1 .. t_f + energy pass of an item; every epilogue warp
+  // arrives after its state writes and proxy fence): the producer copies the tile's
+  // own K slice on it without a round trip through the epoch counter in L2.  Arrivals
+  // and waits pair one to one, so the barrier is never more than one phase ahead.
+  uint64_t own_pub;
   uint64_t drain;
   uint32_t tmem_slot;
   int32_t abort_flag;
@@ -386,7 +392,10 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   // (epilogue warps) * (t + 1) when the whole tile of state S_t is visible.
   ptx::fence_proxy_async_global();
   __syncwarp();
-  if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
+  if (lane == 0) {
+    if (t_f + energy_pass >= 1) ptx::mbar_arrive(ptx::smem_u32(&ctl->own_pub));
+    ptx::red_release_gpu_add(my_flag, 1u);
+  }
 
   // Row constants: with d_i > 0 the accumulator starts at h_i + sigma z d_i so that
   // acc / d_i = (h_i + sum_j J_ij s_j) / d_i + sigma z; a spin with d_i = 0 (no
@@ -463,7 +472,10 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     ptx::tmem_wait_st();
     ptx::fence_proxy_async_global();
     __syncwarp();
-    if (lane == 0) ptx::red_release_gpu_add(my_flag, 1u);
+    if (lane == 0) {
+      if (t + 2 <= t_f + energy_pass) ptx::mbar_arrive(ptx::smem_u32(&ctl->own_pub));  // publication t + 2
+      ptx::red_release_gpu_add(my_flag, 1u);
+    }
     if constexpr (!kDouble) {
       // one accumulator: the next step's bias goes in once this step's product has
       // been read (the draws then overlap the other tiles' publication and the copies)
@@ -534,6 +546,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
     uint32_t stage = 0, phase = 0;  // next ring slot to fill
     uint32_t filled = 0;            // ring slots whose copies were issued (for the drain)
+    uint32_t own_pubs = 0;          // own_pub phases completed by the items before this one
     bool ok = true;
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
@@ -586,7 +599,15 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           uint32_t st = claim_stage;
           int ks2 = kslice_base;
           for (int kb = 0; kb < claimed; ++kb) {  // (issued on abort too, so that the barriers complete)
-            if (ok) ok = wait_block(gflags, nb, ks2, need, lane, seen, &ctl, status, t == 0);
+            if (ok && kb == 0) {
+              // the tile's own slice (ks2 = b), published by this pipeline's epilogue:
+              // own_pub completes once per publication the producer copies from
+              ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.own_pub), (own_pubs + t) & 1u, &ctl, status,
+                                                    t == 0 ? kStartTimeoutNs : kTimeoutNs));
+              if (ok) ptx::fence_proxy_async_global();
+            } else if (ok) {
+              ok = wait_block(gflags, nb, ks2, need, lane, seen, &ctl, status, t == 0);
+            }
 #pragma unroll
             for (int a = 0; a < kAtoms; ++a)
               ptx::tma_load_2d_warp(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
@@ -618,6 +639,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           if (!ok) break;
         }
       }
+      own_pubs += static_cast<uint32_t>(steps);
     }
     if (!ok) {
       // drain: wait (bounded) until every copy issued into the last ring slots has landed
@@ -728,6 +750,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       ptx::mbar_init(ptx::smem_u32(&c.acc_full), 1);
       ptx::mbar_init(ptx::smem_u32(&c.bias_ready[0]), kEpiWarps);
       ptx::mbar_init(ptx::smem_u32(&c.bias_ready[1]), kEpiWarps);
+      ptx::mbar_init(ptx::smem_u32(&c.own_pub), kEpiWarps);
       ptx::mbar_init(ptx::smem_u32(&c.drain), 1);
       c.abort_flag = 0;
     }
