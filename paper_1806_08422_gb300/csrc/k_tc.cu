@@ -12,8 +12,10 @@
 //   - the TMA warp streams 128-deep K slices of J's row block and of S's replica
 //     block into a ring of shared-memory slots (128-byte swizzle); the J slices of
 //     a step start before the step's state is published, and each S slice as soon
-//     as the epoch flag of the row block that wrote it reaches the step, in a fixed
-//     K order that starts with the tile's own slice;
+//     as the row block that wrote it has published the step, in a fixed K order that
+//     starts with the tile's own slice (signalled by a shared-memory barrier that the
+//     tile's own epilogue warps complete; the other slices by the row blocks' epoch
+//     flags);
 //   - the MMA warp issues tcgen05.mma (M = 128, N = BN, K = 16; one elected lane of
 //     the converged warp) into one of two TMEM accumulators, releasing ring slots
 //     and the accumulator with tcgen05.commit;
@@ -541,7 +543,8 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     // ------------------------------------------------------------ TMA producer
     // Per step: claim the first ring slots and start their J slices at once (J
     // does not depend on the previous step), then issue each slot's S slice once its
-    // row block has published the step's state, and stream the rest of the step.
+    // row block has published the step's state (the own block: own_pub; the others:
+    // their epoch counters), and stream the rest of the step.
     // The whole warp runs the loop; one elected lane issues each copy.
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
     uint32_t stage = 0, phase = 0;  // next ring slot to fill
