@@ -188,11 +188,9 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SharedCt
   }
 }
 
-// Warp-wide wait until every row block's epoch counter of one group reaches
-// `need`: lane l polls row blocks l, l+32, ... in parallel.  Returns false (on every
-// lane) on abort/timeout.
 // Row blocks of a group seen published at the current step: lane l holds bit j for
-// row block l + 32 j (a group has at most 152 row blocks, so j < 5).
+// row block l + 32 j (a group has at most 304 row blocks, two pipelines on each of
+// 152 SMs, so j < 10).
 __device__ __forceinline__ bool block_seen(uint32_t seen, int k) {
   return (__shfl_sync(0xffffffffu, seen, k & 31) >> (k >> 5)) & 1u;
 }
