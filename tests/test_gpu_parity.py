@@ -75,6 +75,38 @@ def test_single_step_256_replica_tiles():
         assert (np.abs(out["phi"][sl] - ref["phi"]) / scale).max() <= TOL["bf16"], r0
 
 
+@pytest.mark.parametrize("n,R", [(384, 200), (1100, 256)])
+def test_second_step_reads_every_row_blocks_first_step_state(n, R):
+    # The tensor path's exchange between steps: Phi of step 2 must be the oracle's
+    # single step from the GPU's own state after step 1, for every row block (the
+    # tile's own K slice, signalled inside the CTA, and the other row blocks' slices,
+    # signalled through their epoch counters).  sigma = 0 so the oracle's step from
+    # that state needs no noise of step 2; alpha = 0.5 and a low T_1 move the state far
+    # in step 1, so that a stale slice shows.  n = 384, R = 200: 64-replica tiles,
+    # 3 row blocks; n = 1100, R = 256: 128-replica tiles, 9 row blocks, ragged tail.
+    J = inst.sk(n, 300 + n)
+    s0 = _rand_state(R, n, 301)
+    T = [0.3, 0.5]
+    g = Gpu(J, precision="bf16")
+    s1 = g.run(T[:1], 0.0, 0.5, R, s0=s0, want_state=True)["state"]
+    phi2 = g.run(T, 0.0, 0.5, R, s0=s0, want_phi=True)["phi"]
+    g.close()
+    ref = oracle.run(J, T[1:], 0.0, 0.5, R, s0=s1, want_phi=True)["phi"]
+    d = oracle.row_norms(J)
+    scale = (np.abs(s1) @ np.abs(J).T) / d[None, :]
+    err = np.abs(phi2 - ref) / scale
+    assert err.max() <= TOL["bf16"], float(err.max())
+    # the check would see a tile that read its own row block's state of the step
+    # before: that error is far above the tolerance
+    stale = np.empty_like(ref)
+    for b0 in range(0, n, 128):
+        rows = slice(b0, min(n, b0 + 128))
+        mix = s1.copy()
+        mix[:, rows] = s0[:, rows]
+        stale[:, rows] = (mix @ J[rows, :].T) / d[None, rows]
+    assert (np.abs(stale - ref) / scale).max() > 10 * TOL["bf16"]
+
+
 @pytest.mark.parametrize("prec", DENSE)
 def test_single_step_full_size_sampled(prec):
     # SK N = 2000 with 1024 replicas in the launch configuration of the benchmark;
