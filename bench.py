@@ -12,6 +12,19 @@ HBM; `e2e` is the same metric through the host-buffer C call (nmfa_run) with the
 temperature upload and the sign/energy download inside the timed region.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the workload.
 Multi-GPU: each rank runs its own replicas (weak scaling, no data-path collective).
+
+On rank 0 the line also carries the metric's second half and the other workloads,
+each measured after the timed region (`--no-extra` skips them):
+  time_to_target -- a bounded served leg: Poisson arrivals (200 req/s for 0.5 s, N
+                    log-uniform in [64, 2048], SK or G(N, 0.5), 64-1024 replicas,
+                    FP8-stored J) through the library's server, and the same request
+                    stream through the plain FP32 per-instance path in arrival order:
+                    p50/p99 time-to-target and success fractions of both;
+  c1_fp64        -- SK N = 100, 100 replicas, t_f = 1000 on the FP64 path;
+  c3_csr         -- Moebius ladder N = 2000, int8 CSR, 512 replicas, FP32;
+  c4_ragged      -- 512 instances, N uniform in [16, 1000], 64 replicas each, one
+                    persistent launch replayed from a CUDA graph;
+each with its own roofline fraction.
 """
 from __future__ import annotations
 
@@ -130,11 +143,32 @@ def kernel_traffic():
         return None
 
 
-def cpu_baseline(sample_replicas=48, sample_steps=T_F, nthreads=0):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(sample_replicas=48, sample_steps=T_F, nthreads=0, extra=True):
     """The FP64 oracle (as it stands) on a bounded sample of the workload: the same
     instance and schedule, `sample_replicas` of the 1024 replicas over the first
     `sample_steps` steps (about 10 s of CPU work at the defaults), OpenMP over
-    replicas on every host core."""
+    replicas on every host core.  With `extra`, also the same code on one thread (2
+    replicas x 500 steps) and the plain FP64 workload (SK N = 100, 100 replicas,
+    t_f = 1000) in full on every core."""
     import numpy as np
 
     import oracle
@@ -147,9 +181,182 @@ def cpu_baseline(sample_replicas=48, sample_steps=T_F, nthreads=0):
     oracle.run(J, T, SIGMA, ALPHA, sample_replicas, seed=0, nthreads=cores)
     dt = time.perf_counter() - t0
     units = sample_replicas * N_SPINS * sample_steps
-    return {"value": units / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
-            "sample": "SK N=%d, %d replicas x first %d of %d steps (FP64 C oracle, OpenMP over replicas), %.2f s"
-                      % (N_SPINS, sample_replicas, sample_steps, T_F, dt)}
+    out = {"value": units / dt, "unit": "spin-updates/s", "cores": cores, "kind": "oracle",
+           "sample": "SK N=%d, %d replicas x first %d of %d steps (FP64 C oracle, OpenMP over replicas), %.2f s"
+                     % (N_SPINS, sample_replicas, sample_steps, T_F, dt),
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+    if extra:
+        t0 = time.perf_counter()
+        oracle.run(J, inst.schedule(T_F)[:500], SIGMA, ALPHA, 2, seed=0, nthreads=1)
+        d1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": 2 * N_SPINS * 500 / d1, "unit": "spin-updates/s", "cores": 1,
+                                "sample": "SK N=%d, 2 replicas x first 500 steps, one thread, %.2f s"
+                                          % (N_SPINS, d1)}
+        J1 = inst.sk(100, 0)
+        t0 = time.perf_counter()
+        oracle.run(J1, inst.schedule(T_F), SIGMA, ALPHA, 100, seed=0, nthreads=cores)
+        dc = time.perf_counter() - t0
+        out["c1_full"] = {"value": 100 * 100 * T_F / dc, "unit": "spin-updates/s", "cores": cores,
+                          "sample": "plain FP64 workload in full: SK N=100, 100 replicas, t_f=%d, %.2f s"
+                                    % (T_F, dc)}
+    return out
+
+
+# ------------------------------------------------------------------ other workloads
+# CSR kernel's warp instructions per spin-update on the Moebius ladder N = 2000 with
+# 512 replicas (ncu: smsp__inst_executed.sum / spin-updates,
+# profiles/csr_kernel_moebius2000_r512_tf100_full.md); the issue roofline is four warp
+# instructions per clock on each SM.
+CSR_WARP_INSTR_PER_UPDATE = 3.07
+
+
+def _kernel_ms_runs(prob, reps, run):
+    """Median annealing-kernel time (CUDA events the library records on the run's
+    stream) over `reps` runs after one warm-up run."""
+    from paper_1806_08422_gb300 import nmfa
+
+    nmfa.nmfa_profile_enable(prob.handle, True)
+    run()
+    prob.sync()
+    ms = []
+    for _ in range(reps):
+        run()
+        prob.sync()
+        ms.append(nmfa.nmfa_last_kernel_ms(prob.handle))
+    nmfa.nmfa_profile_enable(prob.handle, False)
+    return statistics.median(ms)
+
+
+def leg_c1_fp64(dev, stream, alu, reps=5):
+    """The plain FP64 configuration: SK N = 100, 100 replicas, t_f = 1000."""
+    import torch
+
+    from paper_1806_08422_gb300 import instances as inst
+    from paper_1806_08422_gb300 import nmfa
+
+    n, R = 100, 100
+    p = nmfa.Problem(inst.sk(n, 0), precision="fp64")
+    T = torch.as_tensor(inst.schedule(T_F), device=dev)
+    signs = torch.empty((R, n), dtype=torch.int8, device=dev)
+    e = torch.empty(R, dtype=torch.int64, device=dev)
+    ms = _kernel_ms_runs(p, reps, lambda: p.run_device(T, SIGMA, ALPHA, R, signs=signs, energy_i64=e, stream=stream))
+    p.close()
+    tflops = 2.0 * n * n * R * T_F / (ms / 1e3) / 1e12
+    pk = alu["fp64_fma_tflops"] if alu else None
+    return {"workload": "SK N=100 J=+-1, 100 replicas, t_f=1000, FP64 CUDA-core path", "kernel_ms": ms,
+            "spin_updates_per_s": n * R * T_F / (ms / 1e3), "us_per_replica_run": 1e3 * ms / R,
+            "min_energy": int(e.min().item()),
+            "roofline": {"bound": "alu", "achieved": tflops, "unit": "TFLOP/s", "peak": pk,
+                         "frac": tflops / pk if pk else None,
+                         "peak_source": "measured FP64 FMA rate (nmfa_measure_alu_peaks)",
+                         "note": "2 n^2 flops per replica-step; 100 CTAs (one replica each) on 152 SMs"}}
+
+
+def leg_c3_csr(dev, stream, sm_mhz, reps=5):
+    """Sparse MAX-CUT: Moebius ladder N = 2000, int8 CSR, 512 replicas, FP32."""
+    import torch
+
+    from paper_1806_08422_gb300 import instances as inst
+    from paper_1806_08422_gb300 import nmfa
+
+    n, R = 2000, 512
+    p = nmfa.Problem(csr=inst.moebius_csr(n), n=n, precision="fp32")
+    T = torch.as_tensor(inst.schedule(T_F), device=dev)
+    signs = torch.empty((R, n), dtype=torch.int8, device=dev)
+    e = torch.empty(R, dtype=torch.int64, device=dev)
+    ms = _kernel_ms_runs(p, reps, lambda: p.run_device(T, SIGMA, ALPHA, R, signs=signs, energy_i64=e, stream=stream))
+    p.close()
+    rate = n * R * T_F / (ms / 1e3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 4 * sm_mhz * 1e6 / CSR_WARP_INSTR_PER_UPDATE
+    return {"workload": "Moebius ladder N=2000 (J=+1 per edge), int8 CSR, 512 replicas, t_f=1000, FP32", "kernel_ms": ms,
+            "spin_updates_per_s": rate, "min_energy": int(e.min().item()), "ground_energy": 4 - 3 * n // 2,
+            "roofline": {"bound": "alu", "achieved": rate, "unit": "spin-updates/s", "peak": peak, "frac": rate / peak,
+                         "peak_source": "instruction issue: %d SMs x 4 warp instructions/clock x %.0f MHz / %.2f warp "
+                                        "instructions per spin-update (ncu count)"
+                                        % (sms, sm_mhz, CSR_WARP_INSTR_PER_UPDATE)}}
+
+
+def leg_c4_ragged(dev, stream, peaks, reps=3, count=512, R=64):
+    """Ragged batch: `count` instances, N uniform in [16, 1000], half SK, half
+    G(N, 0.5) max-cut, R replicas each, one persistent launch replayed from a CUDA
+    graph, tiles from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_1806_08422_gb300 import instances as inst
+    from paper_1806_08422_gb300 import nmfa
+
+    mix = inst.ragged_batch(count, 16, 1000, seed=0)
+    probs = [nmfa.Problem(J, precision="bf16") for _, _, J in mix]
+    T = torch.as_tensor(inst.schedule(T_F), device=dev)
+    energies = [torch.empty(R, dtype=torch.int64, device=dev) for _ in mix]
+    jobs = [nmfa.make_job(T, SIGMA, ALPHA, R, seed=0, stream_id=k, energy_i64=e) for k, e in enumerate(energies)]
+    b = nmfa.nmfa_batch_create([p.handle for p in probs], jobs, nmfa.NMFA_BATCH_GRAPH | nmfa.NMFA_BATCH_AUTOTUNE)
+    try:
+        nmfa.nmfa_batch_launch(b, stream)
+        nmfa.nmfa_batch_sync(b)
+        ms = []
+        for _ in range(reps):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nmfa.nmfa_batch_launch(b, stream)
+            z.record(stream)
+            nmfa.nmfa_batch_sync(b)
+            stream.synchronize()
+            ms.append(a.elapsed_time(z))
+        info = nmfa.nmfa_batch_info(b)
+    finally:
+        nmfa.nmfa_batch_destroy(b)
+        for p in probs:
+            p.close()
+    ns = np.array([n for _, n, _ in mix], dtype=np.float64)
+    npad = np.ceil(ns / 128.0) * 128.0
+    per = statistics.median(ms) / 1e3
+    flops = 2.0 * float((ns ** 2).sum()) * R * (T_F + 1)       # t_f products + the energy product
+    flops_pad = 2.0 * float((npad ** 2).sum()) * R * (T_F + 1)
+    burst = peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained"))
+    achieved = flops / per / 1e12
+    return {"workload": "%d instances, N uniform in [16, 1000] (half SK +-1, half G(N,0.5) max-cut), %d replicas each, "
+                        "t_f=1000, BF16 J/S, FP32 accumulation, one persistent launch from a CUDA graph, autotuned "
+                        "tiles" % (count, R),
+            "ms_per_batch": statistics.median(ms), "spin_updates_per_s": float(ns.sum()) * R * T_F / per,
+            "grid": info["grid"], "groups": info["groups"],
+            "roofline": {"bound": "tensor", "achieved": achieved, "unit": "TFLOP/s", "peak": burst,
+                         "frac": achieved / burst, "peak_source": "bf16_tflops (burst)",
+                         "achieved_at_padded_sizes": flops_pad / per / 1e12,
+                         "note": "algorithmic flops 2 N^2 R (t_f + 1) at each instance's own N; the kernel computes "
+                                 "128-padded tiles"}}
+
+
+def leg_served(rate=200.0, duration=0.5, n_lo=64, n_hi=2048, fp32_cap=30.0):
+    """The metric's second half: p50/p99 time-to-target of a Poisson request stream
+    through the library's server (continuous batching on the tensor path, FP8-stored
+    J) and through the plain FP32 per-instance path in arrival order, same requests,
+    same seeds and noise streams (attempt k draws stream k on both)."""
+    from paper_1806_08422_gb300 import serve
+
+    reqs = serve.make_stream(rate, duration, n_lo, n_hi, seed=0)
+    pool = serve.InstancePool()
+    for r in reqs:
+        pool.get(r["kind"], r["n"])
+    srv = serve.run_server(reqs, pool)
+    f32 = serve.run_fp32_fifo(reqs, pool, time_cap_s=fp32_cap)
+
+    def summary(d, served):
+        return {"p50_s": d["p50_ttt_s"], "p99_s": d["p99_ttt_s"], "requests": d["requests"], "served": served,
+                "succeeded": d["succeeded"], "p_success": d["succeeded"] / max(1, served),
+                "spin_updates_per_s": d["spin_updates_per_s"], "wall_s": d["wall_s"]}
+
+    return {"workload": "Poisson %.0f req/s for %.2f s (%d requests), N log-uniform in [%d, %d] (16 sizes), SK +-1 or "
+                        "G(N,0.5) max-cut, R in {64,...,1024}, t_f=1000; target H <= -0.70 N^1.5 (SK) / -0.34 N^1.5 "
+                        "(G(N,0.5)); up to 4 attempts (attempt k on noise stream k)"
+                        % (rate, duration, len(reqs), n_lo, n_hi),
+            "tensor_server": dict(summary(srv, srv["requests"]), launches=srv["launches"],
+                                  mean_attempts=srv["mean_attempts"], precision="BF16 S, FP8-E4M3-stored J"),
+            "fp32_per_instance": dict(summary(f32, f32["served"]), time_cap_s=fp32_cap,
+                                      note="served one request at a time in arrival order; requests not started "
+                                           "within the cap are not counted")}
 
 
 def bench_config(precision, tf, ws):
@@ -168,11 +375,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_baseline(sample_replicas=16, sample_steps=20)
+        cpu_baseline(sample_replicas=16, sample_steps=20, extra=False)
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(sample_replicas=16, sample_steps=200))
+        vals.append(cpu_baseline(sample_replicas=16, sample_steps=200, extra=False))
     wall = time.perf_counter() - t_all
     units = sum(16 * N_SPINS * 200 for _ in vals)
     value = units / wall
@@ -199,6 +406,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the served leg and the C1/C3/C4 workloads")
     ap.add_argument("--tf", type=int, default=T_F, help="steps per run (profiling of a shorter run)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -339,6 +547,13 @@ def main():
                                            "peak": alu["fp32_fma_tflops"] if alu else None,
                                            "frac": tf32 / alu["fp32_fma_tflops"] if alu else None}}
         p32.close()
+
+    if rank == 0 and not args.no_extra and args.precision == "bf16":
+        sm_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        extra["time_to_target"] = leg_served()
+        extra["c1_fp64"] = leg_c1_fp64(dev, stream, alu)
+        extra["c3_csr"] = leg_c3_csr(dev, stream, sm_mhz)
+        extra["c4_ragged"] = leg_c4_ragged(dev, stream, peaks)
 
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()

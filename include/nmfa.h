@@ -142,13 +142,18 @@ int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
  * not pay for or serialise on cudaMalloc.  The handle itself was allocated by
  * nmfa_create beforehand; this call only reuses it.
  *
- * The tensor kernel's scratch (two BF16 copies of the state and one epoch flag per
- * tile) comes from a static device array of 16 MiB that every GPU loading this
- * library holds until the process exits.  The scratch needed is
- * 4 * ceil(R/BN)*BN * ceil(n/128)*128 bytes plus the flags (BN, the run's tile
- * width, is 64 for R <= 64 and for small problems, else 128); larger sizes return
- * NMFA_EINVAL with nothing launched (e.g. n = 2000 takes up to R = 1920).  The flags are cleared on the stream before each launch;
- * the state buffers are fully written by the kernel before they are read.
+ * The tensor kernel's scratch (two BF16 copies of the state, one epoch flag per
+ * tile, the run plan and the per-replica energy sums) comes from a static device
+ * array of 16 MiB that every GPU loading this library holds until the process
+ * exits.  The rule is: the run's tensor-path workspace must fit in 16 MiB.  The
+ * state alone is 4 * ceil(R/BN)*BN * ceil(n/128)*128 bytes, where BN, the run's
+ * tile width, is 64 (R <= 64, or small problems), 128, or 256 (n >= 1921 when
+ * 128-replica tiles would need more than one wave of the grid); the plan adds a
+ * few tens of KB.  So n = 2000 takes up to R = 1792 (R = 1793 .. 1920 round up to
+ * 2048 replicas, exactly 16 MiB of state, and are refused).  Larger sizes return
+ * NMFA_EINVAL with nothing launched.  The flags and sums are cleared on the stream
+ * before each launch; the state buffers are fully written by the kernel before
+ * they are read.
  *   signs_dev  R*n int8, required (no scratch is made for signs)
  *   energy_dev, energy_i64_dev  as in nmfa_run_device (may be NULL)
  * The first call on a device looks up the array's device address (with that

@@ -36,14 +36,17 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
+    # a per-process temporary name and an atomic rename: several processes (e.g. the
+    # ranks of a multi-process test) may build at once
+    tmp = "%s.%d.tmp" % (_LIB_PATH, os.getpid())
     base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", "-fvisibility=hidden", _SRC, "-o", _LIB_PATH + ".tmp"]
+            "-fno-fast-math", "-fvisibility=hidden", _SRC, "-o", tmp]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], check=True,
                        capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base + ["-lm"], check=True)
-    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
 
@@ -71,10 +74,10 @@ def _load():
         lib.orc_energy.restype = f64
         lib.orc_energy_i64.argtypes = [i32, P, P, P]
         lib.orc_energy_i64.restype = i64
-        lib.orc_run_dense.argtypes = [i32, P, P, P, i32, f64, f64, i32, i64, u64, u32,
+        lib.orc_run_dense.argtypes = [i32, P, P, P, i32, f64, f64, i32, i64, i32, u64, u32,
                                       i32, P, P, P, P, i32]
         lib.orc_run_dense.restype = ctypes.c_int
-        lib.orc_run_csr.argtypes = [i32, P, P, P, P, P, i32, f64, f64, i32, i64, u64,
+        lib.orc_run_csr.argtypes = [i32, P, P, P, P, P, i32, f64, f64, i32, i64, i32, u64,
                                     u32, i32, P, P, P, P, i32]
         lib.orc_run_csr.restype = ctypes.c_int
         lib.orc_brute_force.argtypes = [i32, P, P, P, P]
@@ -141,8 +144,9 @@ def is_integer_problem(J, h=None) -> bool:
 
 
 def run(J, T, sigma, alpha, replicas, seed=0, stream=0, h=None, noise_sign=1, s0=None,
-        want_state=False, want_phi=False, nthreads=0, csr=None, r_first=0):
-    """Algorithm 1 over replicas r_first .. r_first+replicas-1.  Returns a dict with
+        want_state=False, want_phi=False, nthreads=0, csr=None, r_first=0, t_first=0):
+    """Algorithm 1 over replicas r_first .. r_first+replicas-1, its steps drawn as
+    steps t_first .. t_first+len(T)-1 of the noise stream.  Returns a dict with
     signs (R, n) int8, energy (R,) float64, energy_i64 (R,) int64 or None,
     and, on request, state (R, n) and phi (R, n) (the last step's Phi).
 
@@ -168,12 +172,14 @@ def run(J, T, sigma, alpha, replicas, seed=0, stream=0, h=None, noise_sign=1, s0
     phi = np.zeros((replicas, n)) if want_phi else None
     if csr is not None:
         rc = lib.orc_run_csr(n, _ptr(h), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(T),
-                             t_f, float(sigma), float(alpha), int(replicas), int(r_first), int(seed),
+                             t_f, float(sigma), float(alpha), int(replicas), int(r_first), int(t_first),
+                             int(seed),
                              int(stream), int(noise_sign), _ptr(s0), _ptr(state),
                              _ptr(phi), _ptr(signs), int(nthreads))
     else:
         rc = lib.orc_run_dense(n, _ptr(h), _ptr(J), _ptr(T), t_f, float(sigma),
-                               float(alpha), int(replicas), int(r_first), int(seed), int(stream),
+                               float(alpha), int(replicas), int(r_first), int(t_first), int(seed),
+                               int(stream),
                                int(noise_sign), _ptr(s0), _ptr(state), _ptr(phi),
                                _ptr(signs), int(nthreads))
     if rc != 0:

@@ -161,7 +161,9 @@ ORC_EXPORT int64_t orc_energy_i64(int32_t n, const double* h, const double* J,
 /* stored entries of row i in the stored (ascending column) order.              */
 /* s_out / phi_out receive the final state and the last step's Phi (replica-    */
 /* major, r*n + i) when not NULL.  r_first offsets the replica index used for   */
-/* the noise stream, so that any slice of replicas can be recomputed alone.     */
+/* the noise stream, so that any slice of replicas can be recomputed alone;     */
+/* t_first offsets the step index in the same way (T[t] is this call's step t,  */
+/* drawn as step t_first + t), so that a run can be continued from its state.   */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t n;
@@ -185,8 +187,9 @@ static double coupling_sum(const orc_problem* p, int32_t i, const double* s) {
 }
 
 static int run_common(const orc_problem* p, const double* T, int32_t t_f, double sigma,
-                      double alpha, int32_t replicas, int64_t r_first, uint64_t seed,
-                      uint32_t stream, int32_t noise_sign, const double* s0, double* s_out,
+                      double alpha, int32_t replicas, int64_t r_first, int32_t t_first,
+                      uint64_t seed, uint32_t stream, int32_t noise_sign, const double* s0,
+                      double* s_out,
                       double* phi_out, int8_t* signs_out, int32_t nthreads) {
   const int32_t n = p->n;
   double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -215,7 +218,7 @@ static int run_common(const orc_problem* p, const double* T, int32_t t_f, double
       for (int32_t i = 0; i < n; ++i) {
         double P = (p->h ? p->h[i] : 0.0) + coupling_sum(p, i, s);
         double field = (d[i] > 0.0) ? P / d[i] : 0.0;
-        double z = orc_gauss(seed, stream, r_first + r, t, i);
+        double z = orc_gauss(seed, stream, r_first + r, t_first + t, i);
         phi[i] = field + sigma * z * ns;
         sh[i] = -tanh(phi[i] / T[t]);
       }
@@ -238,23 +241,25 @@ static int run_common(const orc_problem* p, const double* T, int32_t t_f, double
 
 ORC_EXPORT int orc_run_dense(int32_t n, const double* h, const double* J, const double* T,
                              int32_t t_f, double sigma, double alpha, int32_t replicas,
-                             int64_t r_first, uint64_t seed, uint32_t stream,
-                             int32_t noise_sign, const double* s0, double* s_out,
-                             double* phi_out, int8_t* signs_out, int32_t nthreads) {
+                             int64_t r_first, int32_t t_first, uint64_t seed,
+                             uint32_t stream, int32_t noise_sign, const double* s0,
+                             double* s_out, double* phi_out, int8_t* signs_out,
+                             int32_t nthreads) {
   orc_problem p = {n, h, J, NULL, NULL, NULL};
-  return run_common(&p, T, t_f, sigma, alpha, replicas, r_first, seed, stream, noise_sign,
-                    s0, s_out, phi_out, signs_out, nthreads);
+  return run_common(&p, T, t_f, sigma, alpha, replicas, r_first, t_first, seed, stream,
+                    noise_sign, s0, s_out, phi_out, signs_out, nthreads);
 }
 
 ORC_EXPORT int orc_run_csr(int32_t n, const double* h, const int64_t* row_ptr,
                            const int32_t* col, const double* val, const double* T,
                            int32_t t_f, double sigma, double alpha, int32_t replicas,
-                           int64_t r_first, uint64_t seed, uint32_t stream,
-                           int32_t noise_sign, const double* s0, double* s_out,
-                           double* phi_out, int8_t* signs_out, int32_t nthreads) {
+                           int64_t r_first, int32_t t_first, uint64_t seed,
+                           uint32_t stream, int32_t noise_sign, const double* s0,
+                           double* s_out, double* phi_out, int8_t* signs_out,
+                           int32_t nthreads) {
   orc_problem p = {n, h, NULL, row_ptr, col, val};
-  return run_common(&p, T, t_f, sigma, alpha, replicas, r_first, seed, stream, noise_sign,
-                    s0, s_out, phi_out, signs_out, nthreads);
+  return run_common(&p, T, t_f, sigma, alpha, replicas, r_first, t_first, seed, stream,
+                    noise_sign, s0, s_out, phi_out, signs_out, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -41,6 +41,55 @@ SIGMAS = (0.1, 0.15, 0.2)
 TABLE_I_DENSITY = -0.73  # Table I's NMFA mean on K2000 as H / N^1.5
 
 
+def sweep(schedules=None, alphas=ALPHAS, sigmas=SIGMAS, n=2000, replicas=256, t_f=1000, ladder_replicas=1000,
+          ladder_t_f=100, seed=0):
+    """Every (schedule, alpha, sigma) setting on SK n (t_f steps) and on the 16-spin
+    Moebius ladder (ladder_t_f steps), all as jobs of ONE batched launch; job k draws
+    noise stream k.  Returns one dict per setting."""
+    import torch
+
+    schedules = SCHEDULES if schedules is None else schedules
+    dev = torch.device("cuda", 0)
+    J = inst.sk(n, seed=seed)
+    ladder = inst.moebius(16)
+    p_sk = nmfa.Problem(J, precision="bf16")
+    p_ld = nmfa.Problem(ladder, precision="bf16")
+    settings, problems, jobs, outs = [], [], [], []
+    for name, knots in schedules.items():
+        for a in alphas:
+            for s in sigmas:
+                for kind, prob, R, tf in (("sk", p_sk, replicas, t_f), ("ladder", p_ld, ladder_replicas, ladder_t_f)):
+                    T = torch.as_tensor(inst.schedule(tf, knots), device=dev)
+                    e = torch.empty(R, dtype=torch.int64, device=dev)
+                    settings.append((name, a, s, kind, tf, len(jobs)))
+                    problems.append(prob.handle)
+                    jobs.append(nmfa.make_job(T, s, a, R, seed=seed, stream_id=len(jobs), energy_i64=e))
+                    outs.append((T, e))
+    b = nmfa.nmfa_batch_create(problems, jobs, 0)
+    try:
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+    finally:
+        nmfa.nmfa_batch_destroy(b)
+    n15 = n ** 1.5
+    rows = {}
+    for (name, a, s, kind, tf, stream), (_, e) in zip(settings, outs):
+        ev = e.cpu().numpy().astype(np.float64)
+        key = (name, a, s)
+        r = rows.setdefault(key, {"schedule": name, "knots": schedules[name], "alpha": a, "sigma": s, "seed": seed})
+        if kind == "sk":
+            dens = ev / n15
+            r.update({"sk_n": n, "sk_t_f": tf, "sk_replicas": len(ev), "sk_stream": stream,
+                      "sk_mean_density": float(dens.mean()), "sk_best_density": float(dens.min()),
+                      "sk_mean_vs_table_I": float(dens.mean() / TABLE_I_DENSITY - 1.0)})
+        else:
+            r.update({"ladder16_t_f": tf, "ladder16_replicas": len(ev), "ladder16_stream": stream,
+                      "ladder16_p_ground": float(np.mean(ev <= -20)), "ladder16_best": int(ev.min())})
+    p_sk.close()
+    p_ld.close()
+    return list(rows.values())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=2000)
@@ -49,48 +98,9 @@ def main():
     ap.add_argument("--ladder-replicas", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
-
-    import torch
-
-    dev = torch.device("cuda", 0)
-    J = inst.sk(args.n, seed=args.seed)
-    ladder = inst.moebius(16)
-    p_sk = nmfa.Problem(J, precision="bf16")
-    p_ld = nmfa.Problem(ladder, precision="bf16")
-    settings, problems, jobs, outs = [], [], [], []
-    for name, knots in SCHEDULES.items():
-        for a in ALPHAS:
-            for s in SIGMAS:
-                for kind, prob, R, tf in (("sk", p_sk, args.replicas, args.t_f),
-                                          ("ladder", p_ld, args.ladder_replicas, 100)):
-                    T = torch.as_tensor(inst.schedule(tf, knots), device=dev)
-                    e = torch.empty(R, dtype=torch.int64, device=dev)
-                    settings.append((name, a, s, kind, tf))
-                    problems.append(prob.handle)
-                    jobs.append(nmfa.make_job(T, s, a, R, seed=args.seed, stream_id=len(jobs), energy_i64=e))
-                    outs.append((T, e))
-    b = nmfa.nmfa_batch_create(problems, jobs, 0)
-    nmfa.nmfa_batch_launch(b)
-    nmfa.nmfa_batch_sync(b)
-    nmfa.nmfa_batch_destroy(b)
-    n15 = args.n ** 1.5
-    rows = {}
-    for (name, a, s, kind, tf), (_, e) in zip(settings, outs):
-        ev = e.cpu().numpy().astype(np.float64)
-        key = (name, a, s)
-        r = rows.setdefault(key, {"schedule": name, "knots": SCHEDULES[name], "alpha": a, "sigma": s})
-        if kind == "sk":
-            dens = ev / n15
-            r.update({"sk_n": args.n, "sk_t_f": tf, "sk_replicas": len(ev), "sk_mean_density": float(dens.mean()),
-                      "sk_best_density": float(dens.min()),
-                      "sk_mean_vs_table_I": float(dens.mean() / TABLE_I_DENSITY - 1.0)})
-        else:
-            r.update({"ladder16_t_f": tf, "ladder16_p_ground": float(np.mean(ev <= -20)),
-                      "ladder16_best": int(ev.min())})
-    for r in rows.values():
+    for r in sweep(n=args.n, replicas=args.replicas, t_f=args.t_f, ladder_replicas=args.ladder_replicas,
+                   seed=args.seed):
         print(json.dumps(r), flush=True)
-    p_sk.close()
-    p_ld.close()
 
 
 if __name__ == "__main__":

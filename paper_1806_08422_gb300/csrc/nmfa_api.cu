@@ -888,8 +888,9 @@ int nmfa_run(nmfa_problem* p, const double* T, int32_t t_f, double sigma, double
 }
 
 // The allocation-free variant of nmfa_run_device for the tensor path: the kernel's
-// scratch comes from a static device array (see launch_tc_static_scratch), signs must
-// be supplied by the caller, and nothing on this path allocates device or host memory.
+// scratch comes from a static device array (see launch_tc_static_scratch) and signs
+// must be supplied by the caller, so this path allocates no device memory.  (The
+// launch plan is still built in host vectors.)
 int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, double sigma, double alpha,
                             int32_t replicas, uint64_t seed, uint32_t stream_id, int8_t* signs_dev,
                             double* energy_dev, int64_t* energy_i64_dev, void* cuda_stream) {

@@ -56,7 +56,11 @@ def quartiles(xs):
     return {"median": float(q[1]), "q25": float(q[0]), "q75": float(q[2])}
 
 
-def run_class(kind, n, samples=10000, t_f=1000, seed=1):
+def sample_energies(kind, n, samples=10000, t_f=1000, seed=1, graph=True):
+    """Anneals `samples` replicas of every instance of one (class, size) in one
+    batched launch (instance k on noise stream k).  Returns the instances, their
+    energies (one int64 array per instance, replica order) and the wall time of
+    the timed launch (a warm-up launch runs first)."""
     import torch
 
     dev = torch.device("cuda", 0)
@@ -66,26 +70,37 @@ def run_class(kind, n, samples=10000, t_f=1000, seed=1):
     energies = [torch.empty(samples, dtype=torch.int64, device=dev) for _ in Js]
     jobs = [nmfa.make_job(T, 0.15, 0.15, samples, seed=seed, stream_id=k, energy_i64=e)
             for k, e in enumerate(energies)]
-    b = nmfa.nmfa_batch_create([p.handle for p in probs], jobs, nmfa.NMFA_BATCH_GRAPH)
-    nmfa.nmfa_batch_launch(b)  # warm-up
-    nmfa.nmfa_batch_sync(b)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nmfa.nmfa_batch_launch(b)
-    nmfa.nmfa_batch_sync(b)
-    wall = time.perf_counter() - t0
-    nmfa.nmfa_batch_destroy(b)
+    b = nmfa.nmfa_batch_create([p.handle for p in probs], jobs, nmfa.NMFA_BATCH_GRAPH if graph else 0)
+    try:
+        nmfa.nmfa_batch_launch(b)  # warm-up
+        nmfa.nmfa_batch_sync(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        wall = time.perf_counter() - t0
+    finally:
+        nmfa.nmfa_batch_destroy(b)
+        for p in probs:
+            p.close()
+    return Js, [e.cpu().numpy() for e in energies], wall
+
+
+def run_class(kind, n, samples=10000, t_f=1000, seed=1, targets=None):
+    """Success probability and TTS99 per instance of one (class, size), summarised as
+    medians and quartiles.  `targets` (one energy per instance) defaults to the
+    lowest energy any sample of the instance found."""
+    Js, energies, wall = sample_energies(kind, n, samples, t_f, seed)
     tau = wall / (samples * len(Js))
     ps, tts = [], []
-    for e in energies:
-        ev = e.cpu().numpy()
-        p = float(np.mean(ev <= ev.min()))
+    for k, ev in enumerate(energies):
+        target = ev.min() if targets is None else targets[k]
+        p = float(np.mean(ev <= target))
         ps.append(p)
         tts.append(tts99(tau, p))
-    for p in probs:
-        p.close()
     return {"class": kind, "n": n, "instances": len(Js), "samples": samples, "tau_us": tau * 1e6,
-            "p": quartiles(ps), "tts99_us": quartiles([x * 1e6 for x in tts])}
+            "p": quartiles(ps), "tts99_us": quartiles([x * 1e6 for x in tts]),
+            "per_instance": [{"p": p, "tts99_us": x * 1e6} for p, x in zip(ps, tts)]}
 
 
 def main():

@@ -23,6 +23,28 @@ def phi_scale(J, s0, h, sigma, seed, stream, t=0, r_first=0):
     return base + sigma * np.abs(z)
 
 
+# Rounding allowances of the update s <- alpha (-tanh(Phi / T)) + (1 - alpha) s per path:
+#   mul   relative error of Phi * (1/T) (the FP32 paths multiply by a binary32 1/T);
+#   tanh  absolute error of the tanh the path uses (FP64 tanh and FP32 tanhf are within
+#         two units in the last place of |tanh| <= 1; the BF16 tensor path uses the MUFU
+#         tanh.approx.f32, whose error is about 2^-11 over the whole range);
+#   round the remaining binary32/binary64 roundings (alpha, 1 - alpha, s0, products, sum).
+UPDATE_EPS = {
+    "fp64": {"mul": 2.0 ** -50, "tanh": 2.0 ** -50, "round": 2.0 ** -50},
+    "fp32": {"mul": 2.0 ** -21, "tanh": 2.0 ** -21, "round": 2.0 ** -21},
+    "bf16": {"mul": 2.0 ** -21, "tanh": 2.0 ** -10, "round": 2.0 ** -21},
+}
+
+
+def update_tol(prec, alpha, T, phi, phi_err=0.0):
+    """Elementwise bound on |s_gpu - s_exact| after one step of Algorithm 1's update
+    s = alpha (-tanh(Phi / T)) + (1 - alpha) s_prev from the same s_prev, when the
+    GPU's Phi differs from the exact one by at most `phi_err` (tanh has slope <= 1,
+    so that error enters as phi_err / T)."""
+    e = UPDATE_EPS[prec]
+    return alpha * ((phi_err + np.abs(phi) * e["mul"]) / T + e["tanh"]) + e["round"]
+
+
 def wilson(k, n, zq=1.959963984540054):
     p = k / n
     den = 1 + zq * zq / n

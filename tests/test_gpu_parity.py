@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1806_08422_gb300 import instances as inst
-from tests.helpers import Gpu, phi_scale, wilson
+from tests.helpers import Gpu, phi_scale, update_tol, wilson
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,22 @@ def test_single_step_phi(prec, n, R):
     scale = phi_scale(J, s0, h, sigma, seed, stream)
     err = np.abs(out["phi"] - ref["phi"]) / np.maximum(scale, 1e-300)
     assert err.max() <= TOL[prec], (prec, float(err.max()))
+    _check_update(prec, alpha, T[0], s0, out, ref, TOL[prec] * scale)
     g.close()
+
+
+def _check_update(prec, alpha, T, s_prev, out, ref, phi_err):
+    """Algorithm 1's Boltzmann update and alpha-mix after one step, element by element:
+    (a) the GPU's new state against the update applied in FP64 to the GPU's own Phi
+    (this isolates the epilogue: a wrong alpha, 1 - alpha, temperature or sign is off
+    by far more than the rounding allowance), and (b) against the oracle's state, with
+    the Phi tolerance carried through tanh."""
+    own = alpha * -np.tanh(out["phi"] / T) + (1.0 - alpha) * s_prev
+    bound_a = update_tol(prec, alpha, T, out["phi"])
+    assert np.all(np.abs(out["state"] - own) <= bound_a), (prec, float(np.max(np.abs(out["state"] - own) / bound_a)))
+    bound_b = update_tol(prec, alpha, T, ref["phi"], phi_err)
+    assert np.all(np.abs(out["state"] - ref["state"]) <= bound_b), (
+        prec, float(np.max(np.abs(out["state"] - ref["state"]) / bound_b)))
 
 
 @pytest.mark.parametrize("n,R", [(300, 200), (1000, 64)])
@@ -50,12 +65,13 @@ def test_single_step_phi_bf16_real_field(n, R):
     J = inst.gnp_maxcut(n, 0.5, 200 + n)
     h = inst.random_fields(n, 0.8, 201)
     s0 = _rand_state(R, n, 202)
-    ref = oracle.run(J, [0.6], 0.15, 0.15, R, seed=77, stream=5, h=h, s0=s0, want_phi=True)
+    ref = oracle.run(J, [0.6], 0.15, 0.15, R, seed=77, stream=5, h=h, s0=s0, want_phi=True, want_state=True)
     g = Gpu(J, h=h, precision="bf16")
-    out = g.run([0.6], 0.15, 0.15, R, seed=77, stream_id=5, s0=s0, want_phi=True)
+    out = g.run([0.6], 0.15, 0.15, R, seed=77, stream_id=5, s0=s0, want_phi=True, want_state=True)
     g.close()
     scale = phi_scale(J, s0, h, 0.15, 77, 5)
     assert (np.abs(out["phi"] - ref["phi"]) / scale).max() <= TOL["bf16"]
+    _check_update("bf16", 0.15, 0.6, s0, out, ref, TOL["bf16"] * scale)
 
 
 def test_single_step_256_replica_tiles():
@@ -66,13 +82,16 @@ def test_single_step_256_replica_tiles():
     J = inst.sk(n, 61)
     s0 = _rand_state(R, n, 62)
     g = Gpu(J, precision="bf16")
-    out = g.run([1.1], 0.15, 0.15, R, seed=3, stream_id=4, s0=s0, want_phi=True)
+    out = g.run([1.1], 0.15, 0.15, R, seed=3, stream_id=4, s0=s0, want_phi=True, want_state=True)
     g.close()
     for r0 in (0, 250, 1020, R - 5):
         sl = slice(r0, r0 + 5)
-        ref = oracle.run(J, [1.1], 0.15, 0.15, 5, seed=3, stream=4, s0=s0[sl], want_phi=True, r_first=r0)
+        ref = oracle.run(J, [1.1], 0.15, 0.15, 5, seed=3, stream=4, s0=s0[sl], want_phi=True, r_first=r0,
+                         want_state=True)
         scale = phi_scale(J, s0[sl], None, 0.15, 3, 4, r_first=r0)
         assert (np.abs(out["phi"][sl] - ref["phi"]) / scale).max() <= TOL["bf16"], r0
+        _check_update("bf16", 0.15, 1.1, s0[sl], {"phi": out["phi"][sl], "state": out["state"][sl]}, ref,
+                      TOL["bf16"] * scale)
 
 
 @pytest.mark.parametrize("n,R", [(384, 200), (1100, 256)])
@@ -107,6 +126,47 @@ def test_second_step_reads_every_row_blocks_first_step_state(n, R):
     assert (np.abs(stale - ref) / scale).max() > 10 * TOL["bf16"]
 
 
+@pytest.mark.parametrize("n,R", [(384, 200), (1100, 256)])
+def test_bf16_five_steps_sigma0(n, R):
+    # Five steps of the tensor path from a random state, sigma = 0, alpha = 0.15 (the
+    # paper's), state after every step against the oracle's:
+    #  (a) step k from the GPU's own state after k - 1 steps (runs are deterministic at
+    #      sigma = 0, so a (k-1)-step run gives exactly that state): Phi within the
+    #      BF16 tolerance and the new state within that tolerance carried through tanh;
+    #  (b) k steps from s0 against the oracle's k steps from s0, within the bound
+    #      e_k = (1 - alpha) e_(k-1) + alpha (dPhi_k / T_k + rounding), where
+    #      dPhi_k = tol scale_k + (|J| e_(k-1)) / d carries the earlier steps' error
+    #      through the coupling sum.
+    J = inst.sk(n, 400 + n)
+    s0 = _rand_state(R, n, 401)
+    # temperatures scaled with sqrt(n - 1) = sum_j |J_ij| / d_i, the factor by which a
+    # state error can grow through one coupling sum, so the bound stays small
+    c = np.sqrt((n - 1) / 383.0)
+    T = [c * x for x in (8.0, 6.0, 5.0, 4.0, 3.0)]
+    alpha = 0.15
+    g = Gpu(J, precision="bf16")
+    runs = [g.run(T[:k], 0.0, alpha, R, s0=s0, want_state=True, want_phi=True) for k in range(1, 6)]
+    g.close()
+    d = oracle.row_norms(J)
+    absJ = np.abs(J)
+    prev_gpu = s0
+    e = np.zeros_like(s0)
+    for k in range(1, 6):
+        out = runs[k - 1]
+        Tk = T[k - 1]
+        one = oracle.run(J, [Tk], 0.0, alpha, R, s0=prev_gpu, want_phi=True, want_state=True)
+        scale = (np.abs(prev_gpu) @ absJ.T) / d[None, :]
+        assert (np.abs(out["phi"] - one["phi"]) / scale).max() <= TOL["bf16"], k
+        _check_update("bf16", alpha, Tk, prev_gpu, out, one, TOL["bf16"] * scale)
+        ref = oracle.run(J, T[:k], 0.0, alpha, R, s0=s0, want_phi=True, want_state=True)
+        dphi = TOL["bf16"] * scale + (e @ absJ.T) / d[None, :]
+        e = (1.0 - alpha) * e + update_tol("bf16", alpha, Tk, ref["phi"], dphi)
+        assert np.all(np.abs(out["state"] - ref["state"]) <= e), (k, float(np.max(np.abs(out["state"] - ref["state"]) / e)))
+        prev_gpu = out["state"]
+    # the bound is tight enough to see a dropped memory term (1 - alpha) s
+    assert np.max(e) < 0.1 * (1.0 - alpha) * np.mean(np.abs(s0))
+
+
 @pytest.mark.parametrize("prec", DENSE)
 def test_single_step_full_size_sampled(prec):
     # SK N = 2000 with 1024 replicas in the launch configuration of the benchmark;
@@ -118,14 +178,16 @@ def test_single_step_full_size_sampled(prec):
     sigma, alpha, seed, stream = 0.15, 0.15, 0, 0
     s0 = _rand_state(R, n, 5)
     g = Gpu(J, precision=prec)
-    out = g.run([1.3], sigma, alpha, R, seed=seed, stream_id=stream, s0=s0, want_phi=True)
+    out = g.run([1.3], sigma, alpha, R, seed=seed, stream_id=stream, s0=s0, want_phi=True, want_state=True)
     for r0 in (0, 100, R - 13):
         sl = slice(r0, r0 + 4)
         ref = oracle.run(J, [1.3], sigma, alpha, 4, seed=seed, stream=stream, s0=s0[sl], want_phi=True,
-                         r_first=r0, nthreads=0)
+                         r_first=r0, nthreads=0, want_state=True)
         scale = phi_scale(J, s0[sl], None, sigma, seed, stream, r_first=r0)
         err = np.abs(out["phi"][sl] - ref["phi"]) / scale
         assert err.max() <= TOL[prec], (prec, r0, float(err.max()))
+        _check_update(prec, alpha, 1.3, s0[sl], {"phi": out["phi"][sl], "state": out["state"][sl]}, ref,
+                      TOL[prec] * scale)
     g.close()
 
 
@@ -276,12 +338,13 @@ def test_csr_single_step(prec):
         csr = inst.to_csr(J)
         h = inst.random_fields(n, 0.4, 17)
         s0 = _rand_state(R, n, 18)
-        ref = oracle.run(None, [0.9], 0.15, 0.15, R, seed=4, h=h, s0=s0, want_phi=True, csr=csr)
+        ref = oracle.run(None, [0.9], 0.15, 0.15, R, seed=4, h=h, s0=s0, want_phi=True, csr=csr, want_state=True)
         g = Gpu(None, h=h, precision=prec, csr=csr, n=n)
-        out = g.run([0.9], 0.15, 0.15, R, seed=4, s0=s0, want_phi=True)
+        out = g.run([0.9], 0.15, 0.15, R, seed=4, s0=s0, want_phi=True, want_state=True)
         scale = phi_scale(J, s0, h, 0.15, 4, 0)
         err = np.abs(out["phi"] - ref["phi"]) / scale
         assert err.max() <= TOL[prec]
+        _check_update(prec, 0.15, 0.9, s0, out, ref, TOL[prec] * scale)
         g.close()
 
 

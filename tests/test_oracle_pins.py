@@ -222,6 +222,51 @@ def test_zero_temperature_sign_dynamics():
     np.testing.assert_array_equal(got, s.astype(np.float64))
 
 
+def test_alpha_mix_memory_over_several_steps():
+    # Algorithm 1 with the paper's alpha = 0.15 < 1 (Sec. II): the (1 - alpha) s memory
+    # term carried over twelve steps, against an independent loop that forms every
+    # field with compensated sums (math.fsum) and applies the update with numpy.  Once
+    # with sigma = 0 and once with sigma = 0.15, the draws given to the loop as inputs
+    # (the stream itself is pinned by the known-answer and step-1 tests above).
+    n, R, steps, alpha = 40, 3, 12, 0.15
+    J = inst.sk(n, 23)
+    h = inst.random_fields(n, 0.4, 24)
+    T = np.geomspace(4.0, 2.0, steps)
+    s0 = np.random.default_rng(25).uniform(-0.6, 0.6, size=(R, n))
+    d = np.array([math.sqrt(math.fsum([h[i] ** 2] + [J[i, j] ** 2 for j in range(n)])) for i in range(n)])
+    for sigma in (0.0, 0.15):
+        got = oracle.run(J, T, sigma, alpha, R, seed=9, stream=2, h=h, s0=s0, want_state=True)["state"]
+        s = s0.copy()
+        for t in range(steps):
+            phi = np.empty((R, n))
+            for r in range(R):
+                for i in range(n):
+                    phi[r, i] = math.fsum([h[i]] + [J[i, j] * s[r, j] for j in range(n)]) / d[i]
+                    phi[r, i] += sigma * oracle.gauss(9, 2, r, t, i)
+            s = alpha * -np.tanh(phi / T[t]) + (1.0 - alpha) * s
+        np.testing.assert_allclose(got, s, rtol=0, atol=1e-12)
+        # the memory term matters here: alpha = 1 (no memory) lands far away
+        nomem = oracle.run(J, T, sigma, 1.0, R, seed=9, stream=2, h=h, s0=s0, want_state=True)["state"]
+        assert np.abs(nomem - s).max() > 0.1
+
+
+def test_run_continues_from_its_state():
+    # Algorithm 1's loop carries only the state from one step to the next, and the
+    # draw of step t depends on t alone: k steps, then the remaining steps from that
+    # state with the step index continued, equal the whole run bit for bit.
+    n, R = 50, 5
+    J = inst.sk(n, 26)
+    h = inst.random_fields(n, 0.3, 27)
+    T = inst.schedule(40)
+    whole = oracle.run(J, T, 0.15, 0.15, R, seed=4, stream=3, h=h, want_state=True)["state"]
+    part = oracle.run(J, T[:17], 0.15, 0.15, R, seed=4, stream=3, h=h, want_state=True)["state"]
+    rest = oracle.run(J, T[17:], 0.15, 0.15, R, seed=4, stream=3, h=h, s0=part, want_state=True, t_first=17)
+    np.testing.assert_array_equal(rest["state"], whole)
+    # without the continued step index the draws repeat steps 0.. and the runs differ
+    wrong = oracle.run(J, T[17:], 0.15, 0.15, R, seed=4, stream=3, h=h, s0=part, want_state=True)["state"]
+    assert np.abs(wrong - whole).max() > 1e-3
+
+
 def test_coupling_product_against_compensated_sum():
     # Algorithm 1's field with sigma = 0 from a given state: Phi = (h + J s)/d.
     n, R = 70, 3
@@ -367,3 +412,20 @@ def test_gset_roundtrip_and_cut_value(tmp_path):
     Jm = inst.moebius(16)
     e, _, _ = oracle.brute_force(Jm)
     assert inst.cut_value(Jm, e) == 22.0
+
+
+# --------------------------------------------------------------------------
+# Time to solution (Sec. III: the common TTS metric of Hamerly et al.): the time
+# to reach the target once with 99 % confidence, TTS99 = tau ln(0.01) / ln(1 - p)
+# for a success probability p < 0.99 per run of duration tau, and tau once p >= 0.99.
+# Values computed by hand.
+# --------------------------------------------------------------------------
+def test_tts99_hand_values():
+    from paper_1806_08422_gb300.tts import tts99
+    assert tts99(1.0, 0.9) == pytest.approx(2.0, rel=1e-15)            # ln 0.01 / ln 0.1 = 2
+    assert tts99(1.0, 0.5) == pytest.approx(6.643856189774724, rel=1e-14)  # log2(100)
+    assert tts99(3.0, 0.99) == 3.0 and tts99(3.0, 1.0) == 3.0          # one run suffices
+    assert tts99(2e-6, 0.0) == math.inf                                 # never succeeds
+    # a rare success: ln(0.01)/ln(1-p) ~ ln(100)/p for small p
+    assert tts99(1.0, 1e-6) == pytest.approx(math.log(100.0) / 1e-6, rel=1e-6)
+    assert tts99(1.0, 0.989) > tts99(1.0, 0.99)

@@ -31,7 +31,9 @@ def test_noalloc_matches_run_device_on_consecutive_calls():
 
     __graft_entry__.build()
     dev = torch.device("cuda", 0)
-    cases = [(inst.sk(300, 1), 200, 4), (inst.gnp_maxcut(130, 0.5, 2), 48, 9)]
+    # n = 300, R = 200 and n = 130, R = 48 take 64-replica tiles; SK n = 2000 with
+    # 1024 replicas takes 128-replica tiles (8 MiB of state in the static array)
+    cases = [(inst.sk(300, 1), 200, 4), (inst.gnp_maxcut(130, 0.5, 2), 48, 9), (inst.sk(2000, 5), 1024, 11)]
     T = torch.as_tensor(inst.schedule(150), device=dev)
     probs = [nmfa.Problem(J, precision="bf16") for J, _, _ in cases]
     refs = []
@@ -54,20 +56,32 @@ def test_noalloc_matches_run_device_on_consecutive_calls():
         p.close()
 
 
-def test_noalloc_refuses_sizes_beyond_the_static_buffer():
+def test_noalloc_size_limit_at_the_boundary():
+    # n = 2000 (n_pad = 2048) with more than one wave of 128-replica tiles takes
+    # 256-replica tiles.  R = 1792 rounds to 7 x 256 replicas, 14 MiB of state plus the
+    # plan: it runs and equals nmfa_run_device.  R = 1793 rounds to 2048 replicas,
+    # exactly 16 MiB of state before the plan: refused, with nothing launched.
     import torch
 
     from paper_1806_08422_gb300 import nmfa
 
     dev = torch.device("cuda", 0)
     p = nmfa.Problem(inst.sk(2000, 3), precision="bf16")
-    R = 2048  # 4 * 2048 * 2048 bytes of state plus flags exceed 16 MiB
-    s, e, ei = _buffers(torch, R, p.n, dev)
-    s.fill_(7)
     T = torch.as_tensor(inst.schedule(10), device=dev)
-    with pytest.raises(nmfa.NmfaError) as exc:
-        nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, signs=s, energy=e, energy_i64=ei)
-    assert exc.value.code == nmfa.NMFA_EINVAL and "16 MiB" in str(exc.value)
-    torch.cuda.synchronize()
-    assert int((s != 7).sum()) == 0  # nothing was launched
+    R = 1792
+    ref = _buffers(torch, R, p.n, dev)
+    p.run_device(T, 0.15, 0.15, R, seed=2, signs=ref[0], energy=ref[1], energy_i64=ref[2])
+    p.sync()
+    got = _buffers(torch, R, p.n, dev)
+    nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, seed=2, signs=got[0], energy=got[1], energy_i64=got[2])
+    p.sync()
+    assert torch.equal(got[0], ref[0]) and torch.equal(got[2], ref[2]) and torch.equal(got[1], ref[1])
+    for R in (1793, 1920):
+        s, e, ei = _buffers(torch, R, p.n, dev)
+        s.fill_(7)
+        with pytest.raises(nmfa.NmfaError) as exc:
+            nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, signs=s, energy=e, energy_i64=ei)
+        assert exc.value.code == nmfa.NMFA_EINVAL and "16 MiB" in str(exc.value)
+        torch.cuda.synchronize()
+        assert int((s != 7).sum()) == 0  # nothing was launched
     p.close()
