@@ -211,7 +211,13 @@ typedef struct nmfa_batch nmfa_batch;
 #define NMFA_BATCH_GRAPH 1    /* capture the batch's launches in a CUDA graph at creation */
 #define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128/256) per job by timing */
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
-#define NMFA_BATCH_BN128 16   /* force 128 replicas per tile (results do not change) */
+#define NMFA_BATCH_BN128 16   /* force 128 replicas per tile, one CTA per tile (results do not change) */
+/* Run 128 replicas per tile as CTA pairs (two CTAs sharing one cta_group::2 MMA of
+ * M = 256, each loading half of every state slice) wherever the problem allows it
+ * (n rounded to 128 is a multiple of 256 and the pairs fit on the grid).  Not the
+ * default: on GB300 the pairs run slower than one CTA per tile for the benchmark
+ * workload.  Results do not change. */
+#define NMFA_BATCH_PAIR128 32
 /* Test only: leave the first group's last row-block tile out of the plan.  Nothing
  * then publishes that tile's state, so the group's other tiles wait for a flag that
  * is never set: their bounded waits give up (within 2 s, 20 s at most),
@@ -235,6 +241,11 @@ int nmfa_batch_sync(nmfa_batch* b);
 /* Persistent grid size, number of replica-block groups, workspace bytes. */
 int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes);
 void nmfa_batch_destroy(nmfa_batch* b);
+/* The batch's persistent launches (one per tile variant present): for launch k,
+ * bn[k] = replicas per tile (64, 128 or 256) and ctas_per_mma[k] = 1, or 2 for CTA
+ * pairs sharing one cta_group::2 MMA.  Writes at most `capacity` entries; *count
+ * receives the number of launches.  Host arrays; any output may be NULL. */
+int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t capacity, int32_t* count);
 
 /* Autotuner entry: the replicas-per-tile (64, 128 or 256) the tensor path would use for
  * `replicas` replicas of this problem, measured once per (n rounded to 128,

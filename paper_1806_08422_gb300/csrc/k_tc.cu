@@ -68,7 +68,7 @@ constexpr int kColsPerWarp = 32;
 // [A atom 0][A atom 1][B atom 0][B atom 1].
 constexpr int kAtoms = 2;
 constexpr int kKSlot = kAtoms * kBK;
-constexpr int kMaxStages = 3;
+constexpr int kMaxStages = 4;
 constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 // Geometry per tile width BN (replicas per tile, the MMA's N: 64, 128 or 256).
 //   Epilogue warps: each serves one TMEM lane quarter and 32 replica columns, so a
@@ -87,17 +87,26 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   ring of 2 slots of 96 KB, and a single accumulator [0, 256) beside the master
 //   state [256, 512): its MMAs (N = 256) run near the full tensor rate, and each
 //   step's bias is written into the accumulator after the update has read it.
-template <int BN>
+//   A CTA PAIR (PAIR = true, 128 replicas) is a cluster of two CTAs that share one
+//   cta_group::2 MMA of M = 256: the pair owns two adjacent row blocks (256 spins) of
+//   a group, each CTA its own block (its TMEM lanes, its epilogue warps, its J rows)
+//   and half of the group's replicas of every S slice (the B operand), so each SM
+//   lands 48 KB of operands per 128-deep K slice instead of 64 KB, and the tensor
+//   core reads 96 instead of 128 bytes per clock from each SM's shared memory (at
+//   the full MMA rate).  Ring of 4 slots of 48 KB; the even CTA issues the MMAs.
+template <int BN, bool PAIR = false>
 struct TcShape {
   static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
   static constexpr int kColsPerWarp = BN == 256 ? 64 : 32;
   static constexpr int kEpiWarps = BN == 256 ? 16 : BN / 8;
-  static constexpr int kSubs = BN == 64 ? 2 : 1;   // tile pipelines per CTA
+  static constexpr int kSubs = (BN == 64 && !PAIR) ? 2 : 1;  // tile pipelines per CTA
   static constexpr int kSubWarps = 2 + kEpiWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
-  static constexpr int kStages = BN == 128 ? 3 : 2;  // ring slots per pipeline
-  static constexpr uint32_t kBAtomBytes = BN * 128;  // one B (S) atom: BN rows x 128 bytes
+  static constexpr int kBRows = PAIR ? BN / 2 : BN;  // replica rows of each B slice in this CTA
+  static constexpr int kStages = PAIR ? 4 : (BN == 128 ? 3 : 2);  // ring slots per pipeline
+  static constexpr uint32_t kBAtomBytes = kBRows * 128;  // one B (S) atom: kBRows rows x 128 bytes
   static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
+  static constexpr int kMmaM = PAIR ? 2 * kBM : kBM;
   static constexpr uint32_t kRingBytes = kStages * kStageBytes;
   static constexpr size_t kSmemBytes = static_cast<size_t>(kSubs) * kRingBytes + 1024;
   static constexpr uint32_t kTmemCols = 512;  // allocated once per CTA
@@ -108,8 +117,8 @@ struct TcShape {
   static_assert(kColMaster + BN <= kSubCols, "TMEM columns");
   static_assert(kEpiWarps * kColsPerWarp == 4 * BN, "every (quarter, column) pair once");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+  static_assert(!PAIR || BN == 128, "CTA pairs take 128-replica tiles");
 };
-constexpr int kMaxSubs = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A pipeline that reaches a new group early waits for the group's other pipelines to
 // finish the groups scheduled before it; that first wait gets a longer bound.
@@ -159,6 +168,10 @@ struct SharedCtl {
   // own K slice on it without a round trip through the epoch counter in L2.  Arrivals
   // and waits pair one to one, so the barrier is never more than one phase ahead.
   uint64_t own_pub;
+  // CTA pairs: completes once per publication of the PEER CTA's tile state (its
+  // epilogue warps arrive from the other CTA), so each CTA copies the pair's other
+  // row block without a round trip through that block's epoch counter.
+  uint64_t pair_pub;
   uint64_t drain;
   uint32_t tmem_slot;
   int32_t abort_flag;
@@ -173,13 +186,17 @@ __device__ __forceinline__ bool aborted(SharedCtl* ctl) {
   return *reinterpret_cast<volatile int32_t*>(&ctl->abort_flag) != 0;
 }
 
-// Bounded mbarrier wait; false if the run is being aborted.
+// Bounded mbarrier wait; false if the run is being aborted.  `cluster`: acquire at
+// cluster scope (barriers that the peer CTA of a pair arrives on).
+__device__ __forceinline__ bool try_bar(uint32_t bar, uint32_t parity, bool cluster) {
+  return cluster ? ptx::mbar_try_wait_cluster(bar, parity) : ptx::mbar_try_wait(bar, parity);
+}
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, SharedCtl* ctl, int32_t* status,
-                                         uint64_t limit_ns = kTimeoutNs) {
-  if (ptx::mbar_try_wait(bar, parity)) return true;
+                                         uint64_t limit_ns = kTimeoutNs, bool cluster = false) {
+  if (try_bar(bar, parity, cluster)) return true;
   const uint64_t t0 = ptx::globaltimer_ns();
   while (true) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (try_bar(bar, parity, cluster)) return true;
     if (aborted(ctl)) return false;
     if (ptx::globaltimer_ns() - t0 > limit_ns) {
       raise_abort(ctl, status);
@@ -240,6 +257,18 @@ __device__ __forceinline__ uint32_t bias_bar(SharedCtl* ctl, uint32_t g) {
   return ptx::smem_u32(&ctl->bias_ready[TcShape<BN>::kDoubleAcc ? (g & 1u) : 0u]);
 }
 
+// Tells the MMA issuer that this warp's part of step g's bias is written: on the
+// CTA's own barrier, or (the odd CTA of a pair) on the even CTA's, which issues the
+// pair's MMAs.
+template <int BN>
+__device__ __forceinline__ void arrive_bias(SharedCtl* ctl, uint32_t g, bool remote) {
+  const uint32_t bar = bias_bar<BN>(ctl, g);
+  if (remote)
+    ptx::mbar_arrive_cluster(ptx::mapa_shared(bar, 0u));
+  else
+    ptx::mbar_arrive(bar);
+}
+
 // (A) the bias of one step, h_i + sigma z d_i, written into the accumulator the step
 // will use (the Gaussian draws do not depend on the state, so with two accumulators
 // this runs while the tensor core still computes the previous step), then signalled
@@ -247,7 +276,7 @@ __device__ __forceinline__ uint32_t bias_bar(SharedCtl* ctl, uint32_t g) {
 template <int BN>
 __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base, int col0, int rbase, int i,
                                            uint32_t stream, const RoundKeys& rk, float sigma_ns, float dd, float hi,
-                                           int lane, SharedCtl* ctl) {
+                                           int lane, SharedCtl* ctl, bool remote) {
   const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll 1
@@ -267,13 +296,13 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
-  if (lane == 0) ptx::mbar_arrive(bias_bar<BN>(ctl, g));
+  if (lane == 0) arrive_bias<BN>(ctl, g, remote);
 }
 
 // (A') the accumulator start of the energy product: 2 h_i, no noise.
 template <int BN>
 __device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base, int col0, float hi, int lane,
-                                                  SharedCtl* ctl) {
+                                                  SharedCtl* ctl, bool remote) {
   const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll
@@ -283,7 +312,19 @@ __device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
-  if (lane == 0) ptx::mbar_arrive(bias_bar<BN>(ctl, g));
+  if (lane == 0) arrive_bias<BN>(ctl, g, remote);
+}
+
+// Publication of this tile's state (every epilogue warp, after its state writes and
+// proxy fence): the CTA's own producer (own_pub), the peer CTA's producer of a pair
+// (its pair_pub), then the tile's epoch counter for every other tile of the group.
+template <bool PAIR>
+__device__ __forceinline__ void publish(SharedCtl* ctl, uint32_t* my_flag, bool to_producers, uint32_t crank) {
+  if (to_producers) {
+    ptx::mbar_arrive(ptx::smem_u32(&ctl->own_pub));
+    if constexpr (PAIR) ptx::mbar_arrive_cluster(ptx::mapa_shared(ptx::smem_u32(&ctl->pair_pub), crank ^ 1u));
+  }
+  ptx::red_release_gpu_add(my_flag, 1u);
 }
 
 // (C) Energy readout (Eq. 1) of one warp's 32 spins x 32 replicas.  The accumulator
@@ -345,9 +386,10 @@ __device__ __noinline__ void energy_readout(const TcGroup* __restrict__ g, uint3
 // q = (e + QOFF) % 4 (spins 32q..32q+31 of the tile); it serves that quarter and
 // column group e / 4 (32 replicas), 16 columns per tcgen05.ld.  `gstep` counts the CTA's steps across items
 // (the parity of the accumulator barriers).  Returns false on abort.
-template <int BN, int QOFF>
+template <int BN, int QOFF, bool PAIR>
 __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
-                                              SharedCtl* ctl, int32_t* status, uint32_t& gstep) {
+                                              SharedCtl* ctl, int32_t* status, uint32_t& gstep, uint32_t crank) {
+  const bool remote_bias = PAIR && crank != 0u;
   constexpr int kCW = TcShape<BN>::kColsPerWarp;
   constexpr bool kDouble = TcShape<BN>::kDoubleAcc;
   constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1, kColMaster = TcShape<BN>::kColMaster;
@@ -369,7 +411,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   double* phi_out = g->phi_out;
   __nv_bfloat16* S16 = g->S16;
   uint32_t* my_flag = g->flags + b;
-  uint32_t v[16], m[16];
+  uint32_t m[16];
 
   // the initial state (zero, or the given s0) -> master in TMEM and BF16 buffer 0
   const double* s0 = g->s0;
@@ -392,10 +434,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   // (epilogue warps) * (t + 1) when the whole tile of state S_t is visible.
   ptx::fence_proxy_async_global();
   __syncwarp();
-  if (lane == 0) {
-    if (t_f + energy_pass >= 1) ptx::mbar_arrive(ptx::smem_u32(&ctl->own_pub));
-    ptx::red_release_gpu_add(my_flag, 1u);
-  }
+  if (lane == 0) publish<PAIR>(ctl, my_flag, t_f + energy_pass >= 1, crank);
 
   // Row constants: with d_i > 0 the accumulator starts at h_i + sigma z d_i so that
   // acc / d_i = (h_i + sum_j J_ij s_j) / d_i + sigma z; a spin with d_i = 0 (no
@@ -404,7 +443,8 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   const float sc = inv_d > 0.0f ? inv_d : 1.0f;
   // (A) the bias of step t: the Gaussian draws do not depend on the state, so they
   // are generated while the tensor core still computes the previous step
-  if (t_f > 0) write_bias<BN>(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+  if (t_f > 0)
+    write_bias<BN>(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl, remote_bias);
 
   for (int t = 0; t < t_f; ++t, ++gstep) {
     float inv_T = 0.0f;
@@ -414,9 +454,10 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     // the next step's bias goes into the other accumulator (read last two steps ago)
     if constexpr (kDouble) {
       if (t + 1 < t_f)
-        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
+                       remote_bias);
       else if (energy_pass)
-        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
+        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
     }
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
@@ -472,17 +513,16 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     ptx::tmem_wait_st();
     ptx::fence_proxy_async_global();
     __syncwarp();
-    if (lane == 0) {
-      if (t + 2 <= t_f + energy_pass) ptx::mbar_arrive(ptx::smem_u32(&ctl->own_pub));  // publication t + 2
-      ptx::red_release_gpu_add(my_flag, 1u);
-    }
+    // publication t + 1 (the producers copy it only if another step follows)
+    if (lane == 0) publish<PAIR>(ctl, my_flag, t + 2 <= t_f + energy_pass, crank);
     if constexpr (!kDouble) {
       // one accumulator: the next step's bias goes in once this step's product has
       // been read (the draws then overlap the other tiles' publication and the copies)
       if (t + 1 < t_f)
-        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl);
+        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
+                       remote_bias);
       else if (energy_pass)
-        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl);
+        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
     }
   }
   // sign readout of Algorithm 1: sign of the FP32 master state, zero reads as +1
@@ -519,48 +559,70 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
 
 // One tile pipeline of the persistent kernel: its TMA warp (lw 0), MMA warp (lw 1) and
 // epilogue warps (lw 2..), its control block, ring slots, TMEM columns and work list
-// (plan slot SUB * gridDim.x + blockIdx.x).  SUB is a template argument so that the
-// control block's shared-memory address stays a constant.
-template <int BN, int SUB>
+// (plan slot SUB * gridDim.x + blockIdx.x; for CTA pairs the cluster's slot, shared by
+// both CTAs).  SUB is a template argument so that the control block's shared-memory
+// address stays a constant.
+//
+// K order: every tile of a group sweeps the group's K slices (row blocks) starting at
+// its pair-aligned row block (b & ~1) and wrapping; the two tiles of a CTA pair share
+// one MMA and therefore one order, and every tile variant uses the same rule, so the
+// FP32 sums of every output (and with them the results) do not depend on the variant.
+template <int BN, int SUB, bool PAIR>
 __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items,
                                              const int32_t* __restrict__ first, int32_t* status, SharedCtl* ctl_all,
                                              uint32_t ring_base, uint32_t tmem_base, int warp, int lane) {
-  constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
-  constexpr int kSubWarps = TcShape<BN>::kSubWarps;
-  constexpr int kStages = TcShape<BN>::kStages;
-  constexpr uint32_t kStageBytes = TcShape<BN>::kStageBytes, kBAtomBytes = TcShape<BN>::kBAtomBytes;
-  constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1;
+  using Shape = TcShape<BN, PAIR>;
+  constexpr int kEpiWarps = Shape::kEpiWarps;
+  constexpr int kSubWarps = Shape::kSubWarps;
+  constexpr int kStages = Shape::kStages;
+  constexpr uint32_t kStageBytes = Shape::kStageBytes, kBAtomBytes = Shape::kBAtomBytes;
+  constexpr uint32_t kColAcc1 = Shape::kColAcc1;
   SharedCtl& ctl = ctl_all[SUB];
   const int lw = warp - SUB * kSubWarps;
-  const int slot = SUB * static_cast<int>(gridDim.x) + static_cast<int>(blockIdx.x);
+  const uint32_t crank = PAIR ? ptx::cluster_ctarank() : 0u;
+  const int slot = PAIR ? static_cast<int>(blockIdx.x >> 1)
+                        : SUB * static_cast<int>(gridDim.x) + static_cast<int>(blockIdx.x);
   const int w_begin = first[slot], w_end = first[slot + 1];
-  const uint32_t ring = ring_base + static_cast<uint32_t>(SUB) * TcShape<BN>::kRingBytes;
-  const uint32_t tmem = tmem_base + static_cast<uint32_t>(SUB) * TcShape<BN>::kSubCols;
+  const uint32_t ring = ring_base + static_cast<uint32_t>(SUB) * Shape::kRingBytes;
+  const uint32_t tmem = tmem_base + static_cast<uint32_t>(SUB) * Shape::kSubCols;
 
   if (lw == 0) {
     // ------------------------------------------------------------ TMA producer
     // Per step: claim the first ring slots and start their J slices at once (J
     // does not depend on the previous step), then issue each slot's S slice once its
-    // row block has published the step's state (the own block: own_pub; the others:
-    // their epoch counters), and stream the rest of the step.
-    // The whole warp runs the loop; one elected lane issues each copy.
+    // row block has published the step's state (the own block: own_pub; the pair's
+    // other block: pair_pub; the others: their epoch counters), and stream the rest
+    // of the step.  The whole warp runs the loop; one elected lane issues each copy.
+    // In a pair the even CTA's full barriers count both CTAs' copies (the odd CTA's
+    // copies complete on them); each CTA waits on its own empty barriers, which the
+    // pair's MMA commits signal in both CTAs.
     const uint32_t full0 = ptx::smem_u32(&ctl.full[0]), empty0 = ptx::smem_u32(&ctl.empty[0]);
+    const uint32_t full0_lead = PAIR ? ptx::mapa_shared(full0, 0u) : full0;
+    const bool lead = crank == 0u;
     uint32_t stage = 0, phase = 0;  // next ring slot to fill
     uint32_t filled = 0;            // ring slots whose copies were issued (for the drain)
-    uint32_t own_pubs = 0;          // own_pub phases completed by the items before this one
+    uint32_t own_pubs = 0;          // own_pub (and pair_pub) phases completed by earlier items
     bool ok = true;
+    auto load = [&](uint32_t dst, const void* tm, int x, int y, uint32_t st) {
+      if (PAIR && !lead)
+        ptx::tma_load_2d_pair_warp(dst, tm, x, y, full0_lead + 8u * st);
+      else
+        ptx::tma_load_2d_warp(dst, tm, x, y, full0 + 8u * st);
+    };
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
-      const int b = item.b, n_pad = g->n_pad, nb = n_pad / kBM, bn = g->bn, steps = g->t_f + g->energy_pass;
+      const int b = PAIR ? 2 * item.b + static_cast<int>(crank) : item.b;  // this CTA's row block
+      const int n_pad = g->n_pad, nb = n_pad / kBM, bn = g->bn, steps = g->t_f + g->energy_pass;
       const void* tmJ = &g->tmJ;
       const void* tmS = &g->tmS;
       const uint32_t* gflags = g->flags;
-      const uint32_t stage_tx = kAtoms * (kABytes + static_cast<uint32_t>(bn) * 128u);
+      // bytes that complete one slot's full barrier: both CTAs' copies for a pair
+      const uint32_t stage_tx = (PAIR ? 2u : 1u) * kAtoms *
+                                (kABytes + static_cast<uint32_t>(PAIR ? bn / 2 : bn) * 128u);
+      const int brow = PAIR ? static_cast<int>(crank) * (bn / 2) : 0;  // this CTA's replica rows of S
       const int KB = n_pad / kKSlot;  // ring slots per step (= row blocks)
-      // every row block starts its K sweep at its own 128-deep slice (b) to spread the
-      // CTAs' reads of J and S over L2
-      const int kslice_base = b % KB;
+      const int kslice_base = (b & ~1) % KB;
       if (lane == 0) {
         acquire_tensormap(tmJ);
         acquire_tensormap(tmS);
@@ -570,18 +632,16 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       __syncwarp();
       const int pre = KB < kStages ? KB : kStages;
       for (int t = 0; t < steps && ok; ++t) {
-        const int sy = (t & 1) * bn;
+        const int sy = (t & 1) * bn + brow;
         const uint32_t claim_stage = stage;
         int claimed = 0;
         int ks = kslice_base;  // K slice of loop index kb
         for (int kb = 0; kb < pre; ++kb) {
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
-          ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
+          if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
 #pragma unroll
-          for (int a = 0; a < kAtoms; ++a)
-            ptx::tma_load_2d_warp(ring + stage * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM,
-                                  full0 + 8u * stage);
+          for (int a = 0; a < kAtoms; ++a) load(ring + stage * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, stage);
           ++claimed;
           ++filled;
           if (++stage == kStages) {
@@ -591,28 +651,32 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           if (++ks == KB) ks = 0;
         }
         // Each S half is copied as soon as its own row block has published the step, in
-        // the fixed K order (so the FP32 sums keep one order): the tile's own slice
-        // first, right after this tile's epilogue, then the others, so that the MMAs on
-        // early blocks overlap the wait for a late one.
+        // the fixed K order (so the FP32 sums keep one order): the tile's own slice and
+        // (pairs) the pair's other slice on shared-memory barriers, the others on their
+        // epoch counters, so that the MMAs on early blocks overlap the wait for a late one.
         const uint32_t need = static_cast<uint32_t>(kEpiWarps * (t + 1));
         uint32_t seen = 0;
         {
           uint32_t st = claim_stage;
           int ks2 = kslice_base;
           for (int kb = 0; kb < claimed; ++kb) {  // (issued on abort too, so that the barriers complete)
-            if (ok && kb == 0) {
-              // the tile's own slice (ks2 = b), published by this pipeline's epilogue:
-              // own_pub completes once per publication the producer copies from
+            if (ok && ks2 == b) {
+              // the tile's own slice, published by this pipeline's epilogue: own_pub
+              // completes once per publication the producer copies from
               ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.own_pub), (own_pubs + t) & 1u, &ctl, status,
                                                     t == 0 ? kStartTimeoutNs : kTimeoutNs));
+              if (ok) ptx::fence_proxy_async_global();
+            } else if (PAIR && ok && ks2 == (b ^ 1)) {
+              // the pair's other row block, published by the peer CTA's epilogue
+              ok = __all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl.pair_pub), (own_pubs + t) & 1u, &ctl, status,
+                                                    t == 0 ? kStartTimeoutNs : kTimeoutNs, true));
               if (ok) ptx::fence_proxy_async_global();
             } else if (ok) {
               ok = wait_block(gflags, nb, ks2, need, lane, seen, &ctl, status, t == 0);
             }
 #pragma unroll
             for (int a = 0; a < kAtoms; ++a)
-              ptx::tma_load_2d_warp(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS,
-                                    ks2 * kKSlot + a * kBK, sy, full0 + 8u * st);
+              load(ring + st * kStageBytes + kAtoms * kABytes + a * kBAtomBytes, tmS, ks2 * kKSlot + a * kBK, sy, st);
             if (++st == kStages) st = 0;
             if (++ks2 == KB) ks2 = 0;
           }
@@ -622,15 +686,13 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
           const uint32_t sA = ring + stage * kStageBytes;
-          ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
+          if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
 #pragma unroll
-          for (int a = 0; a < kAtoms; ++a)
-            ptx::tma_load_2d_warp(sA + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, full0 + 8u * stage);
+          for (int a = 0; a < kAtoms; ++a) load(sA + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, stage);
           ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
 #pragma unroll
           for (int a = 0; a < kAtoms; ++a)
-            ptx::tma_load_2d_warp(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy,
-                                  full0 + 8u * stage);
+            load(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy, stage);
           ++filled;
           if (++stage == kStages) {
             stage = 0;
@@ -643,12 +705,19 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       own_pubs += static_cast<uint32_t>(steps);
     }
     if (!ok) {
-      // drain: wait (bounded) until every copy issued into the last ring slots has landed
+      // drain: wait (bounded) until every copy issued into the last ring slots has
+      // landed.  A pair's copies complete on the even CTA's full barriers, so the odd
+      // CTA waits for its own slots to be released by the MMA commits instead.
       const uint32_t last = filled;
       for (uint32_t k = (last > static_cast<uint32_t>(kStages) ? last - kStages : 0u); k < last; ++k) {
         const uint32_t st = k % kStages, ph = (k / kStages) & 1u;
         const uint64_t t0 = ptx::globaltimer_ns();
-        while (!ptx::mbar_try_wait(full0 + 8u * st, ph) && ptx::globaltimer_ns() - t0 < kDrainNs) {
+        if (PAIR && !lead) {
+          while (!ptx::mbar_try_wait(empty0 + 8u * st, ph) && ptx::globaltimer_ns() - t0 < kDrainNs) {
+          }
+        } else {
+          while (!ptx::mbar_try_wait(full0 + 8u * st, ph) && ptx::globaltimer_ns() - t0 < kDrainNs) {
+          }
         }
       }
     }
@@ -659,6 +728,9 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     // shared-memory descriptors are formed once and advanced by adding to their
     // start-address field (32 bytes per K = 16 step, one atom or slot further on; the
     // field cannot carry out of its 14 bits because shared addresses stay below 256 KB).
+    // A pair's MMAs (M = 256 across both CTAs) are issued by the even CTA alone; its
+    // commits arrive on the barriers of both CTAs.
+    if (PAIR && crank != 0u) return;
     uint32_t stage = 0, phase = 0, gstep = 0;
     bool ok = true;
     bool issued = false;
@@ -670,13 +742,14 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       const TcGroup* g = groups + items[w].group;
       const int KB = g->n_pad / kKSlot, steps = g->t_f + g->energy_pass;
       // every group of a plan has the kernel's tile width: N = BN
-      constexpr uint32_t idesc = ptx::idesc_bf16_f32(kBM, BN);
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32(Shape::kMmaM, BN);
       for (int t = 0; t < steps && ok; ++t, ++gstep) {
         // the epilogue has written this step's bias (h + sigma z d) into the
-        // accumulator the step uses; the product accumulates onto it
+        // accumulator the step uses (in both CTAs of a pair); the product
+        // accumulates onto it
         ok = __all_sync(0xffffffffu, wait_bar(bias_bar<BN>(&ctl, gstep),
-                                              TcShape<BN>::kDoubleAcc ? ((gstep >> 1) & 1u) : (gstep & 1u), &ctl,
-                                              status));
+                                              Shape::kDoubleAcc ? ((gstep >> 1) & 1u) : (gstep & 1u), &ctl, status,
+                                              kTimeoutNs, PAIR));
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t acc = tmem + ((gstep & 1u) ? kColAcc1 : 0u);
@@ -689,23 +762,37 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           for (int a = 0; a < kAtoms; ++a) {
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
-              ptx::mma_bf16_warp(acc, da + kDescA * a + kDescK * kk, da + kDescB + kDescBAtom * a + kDescK * kk, idesc);
+              if constexpr (PAIR)
+                ptx::mma_bf16_pair_warp(acc, da + kDescA * a + kDescK * kk, da + kDescB + kDescBAtom * a + kDescK * kk,
+                                        idesc);
+              else
+                ptx::mma_bf16_warp(acc, da + kDescA * a + kDescK * kk, da + kDescB + kDescBAtom * a + kDescK * kk,
+                                   idesc);
             }
           }
           issued = true;
-          ptx::mma_commit_warp(empty0 + 8u * stage);
+          if constexpr (PAIR)
+            ptx::mma_commit_pair_warp(empty0 + 8u * stage, 0x3);
+          else
+            ptx::mma_commit_warp(empty0 + 8u * stage);
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (!ok) break;
-        ptx::mma_commit_warp(ptx::smem_u32(&ctl.acc_full));
+        if constexpr (PAIR)
+          ptx::mma_commit_pair_warp(ptx::smem_u32(&ctl.acc_full), 0x3);
+        else
+          ptx::mma_commit_warp(ptx::smem_u32(&ctl.acc_full));
       }
     }
     if (!ok && issued) {
       // drain: wait (bounded) for every MMA issued so far
-      ptx::mma_commit_warp(ptx::smem_u32(&ctl.drain));
+      if constexpr (PAIR)
+        ptx::mma_commit_pair_warp(ptx::smem_u32(&ctl.drain), 0x1);
+      else
+        ptx::mma_commit_warp(ptx::smem_u32(&ctl.drain));
       const uint64_t t0 = ptx::globaltimer_ns();
       while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.drain), 0u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
       }
@@ -721,20 +808,21 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
-      ok = epilogue_item<BN, (2 + SUB * kSubWarps) & 3>(g, item.b, e, lane, tmem, &ctl, status, gstep);
+      const int b = PAIR ? 2 * item.b + static_cast<int>(crank) : item.b;
+      ok = epilogue_item<BN, (2 + SUB * kSubWarps) & 3, PAIR>(g, b, e, lane, tmem, &ctl, status, gstep, crank);
     }
   }
-
 }
 
-template <int BN>
-__global__ void __launch_bounds__(TcShape<BN>::kThreads, 1)
+template <int BN, bool PAIR = false>
+__global__ void __launch_bounds__(TcShape<BN, PAIR>::kThreads, 1)
 nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
                int32_t* status) {
-  constexpr int kEpiWarps = TcShape<BN>::kEpiWarps;
-  constexpr int kSubs = TcShape<BN>::kSubs, kSubWarps = TcShape<BN>::kSubWarps;
-  constexpr int kStages = TcShape<BN>::kStages;
-  constexpr uint32_t kTmemCols = TcShape<BN>::kTmemCols;
+  using Shape = TcShape<BN, PAIR>;
+  constexpr int kEpiWarps = Shape::kEpiWarps;
+  constexpr int kSubs = Shape::kSubs, kSubWarps = Shape::kSubWarps;
+  constexpr int kStages = Shape::kStages;
+  constexpr uint32_t kTmemCols = Shape::kTmemCols;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   __shared__ SharedCtl ctl_all[kSubs];
 
@@ -749,37 +837,54 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
         ptx::mbar_init(ptx::smem_u32(&c.empty[s]), 1);
       }
       ptx::mbar_init(ptx::smem_u32(&c.acc_full), 1);
-      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[0]), kEpiWarps);
-      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[1]), kEpiWarps);
+      // a pair's MMA issuer waits for the bias of both CTAs' epilogue warps
+      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[0]), (PAIR ? 2 : 1) * kEpiWarps);
+      ptx::mbar_init(ptx::smem_u32(&c.bias_ready[1]), (PAIR ? 2 : 1) * kEpiWarps);
       ptx::mbar_init(ptx::smem_u32(&c.own_pub), kEpiWarps);
+      ptx::mbar_init(ptx::smem_u32(&c.pair_pub), kEpiWarps);
       ptx::mbar_init(ptx::smem_u32(&c.drain), 1);
       c.abort_flag = 0;
     }
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc<kTmemCols>(ptx::smem_u32(&ctl_all[0].tmem_slot));
-    ptx::tmem_relinquish();
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates together
+      ptx::tmem_alloc_pair<kTmemCols>(ptx::smem_u32(&ctl_all[0].tmem_slot));
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc<kTmemCols>(ptx::smem_u32(&ctl_all[0].tmem_slot));
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
+  // a pair's CTAs start once both have initialised their barriers and allocated
+  if constexpr (PAIR) ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem_base = ctl_all[0].tmem_slot;
 
   if constexpr (kSubs == 1) {
-    run_pipeline<BN, 0>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+    run_pipeline<BN, 0, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
   } else {
     if (warp < kSubWarps)
-      run_pipeline<BN, 0>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+      run_pipeline<BN, 0, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
     else
-      run_pipeline<BN, 1>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+      run_pipeline<BN, 1, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
   }
 
   ptx::tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair leaves (or frees its tensor memory) while the pair's MMAs
+  // may still read its shared memory or write its tensor memory: every wait above is
+  // bounded, so both CTAs reach this barrier
+  if constexpr (PAIR) ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc<kTmemCols>(tmem_base);
+    if constexpr (PAIR)
+      ptx::tmem_dealloc_pair<kTmemCols>(tmem_base);
+    else
+      ptx::tmem_dealloc<kTmemCols>(tmem_base);
   }
 }
 
@@ -825,41 +930,64 @@ int make_map_bf16(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols
   return NMFA_OK;
 }
 
-template <int BN>
-int co_resident_ctas_bn(int* capacity) {
+// Co-resident scheduling units of the persistent grid for one tile variant: CTAs
+// (one per SM), or for CTA pairs the clusters of two that fit at once.
+template <int BN, bool PAIR>
+int co_resident_units_t(int* capacity) {
   static int cached = -1;
   if (cached < 0) {
+    using Shape = TcShape<BN, PAIR>;
     int rc;
-    if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(TcShape<BN>::kSmemBytes)),
+    if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(Shape::kSmemBytes)),
                          "tensor kernel attribute")))
       return rc;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN>,
-                                                                       TcShape<BN>::kThreads,
-                                                                       TcShape<BN>::kSmemBytes),
-                         "occupancy")))
-      return rc;
-    // never more CTAs on an SM than its TMEM holds (each allocates kTmemCols of 512)
-    per_sm = std::min(per_sm, static_cast<int>(512 / TcShape<BN>::kTmemCols));
-    cached = per_sm * sms;
+    if constexpr (PAIR) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(static_cast<unsigned>(2 * (sms / 2)), 1, 1);
+      cfg.blockDim = dim3(Shape::kThreads, 1, 1);
+      cfg.dynamicSmemBytes = Shape::kSmemBytes;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if ((rc = cuda_error(cudaOccupancyMaxActiveClusters(&clusters, nmfa_tc_kernel<BN, PAIR>, &cfg),
+                           "cluster occupancy")))
+        return rc;
+      cached = std::min(clusters, sms / 2);
+    } else {
+      if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN, PAIR>,
+                                                                         Shape::kThreads, Shape::kSmemBytes),
+                           "occupancy")))
+        return rc;
+      // never more CTAs on an SM than its TMEM holds (each allocates kTmemCols of 512)
+      per_sm = std::min(per_sm, static_cast<int>(512 / Shape::kTmemCols));
+      cached = per_sm * sms;
+    }
   }
   *capacity = cached;
   return NMFA_OK;
 }
-int co_resident_ctas(int bn, int* capacity) {
-  return bn == 64 ? co_resident_ctas_bn<64>(capacity)
-                  : bn == 256 ? co_resident_ctas_bn<256>(capacity) : co_resident_ctas_bn<128>(capacity);
+int co_resident_units(int bn, bool pair, int* capacity) {
+  if (pair) return co_resident_units_t<128, true>(capacity);
+  return bn == 64 ? co_resident_units_t<64, false>(capacity)
+                  : bn == 256 ? co_resident_units_t<256, false>(capacity) : co_resident_units_t<128, false>(capacity);
 }
-// Work-list slots (tile pipelines) of the co-resident grid.
-int tc_subs(int bn) { return bn == 64 ? TcShape<64>::kSubs : 1; }
-int co_resident_slots(int bn, int* slots) {
-  int ctas = 0;
-  const int rc = co_resident_ctas(bn, &ctas);
+// Tile pipelines per scheduling unit.
+int tc_subs(int bn, bool pair) { return (bn == 64 && !pair) ? TcShape<64>::kSubs : 1; }
+// Work-list slots of the co-resident grid: tile pipelines, or CTA pairs.
+int co_resident_slots(int bn, bool pair, int* slots) {
+  int units = 0;
+  const int rc = co_resident_units(bn, pair, &units);
   if (rc) return rc;
-  *slots = ctas * tc_subs(bn);
+  *slots = units * tc_subs(bn, pair);
   return NMFA_OK;
 }
 
@@ -896,6 +1024,24 @@ int tc_pick_bn(int32_t replicas, int32_t n_pad) {
   return 128;
 }
 
+// Whether 128-replica tiles of an n_pad problem CAN run as CTA pairs (one
+// cta_group::2 MMA of M = 256 per pair of adjacent row blocks): the row blocks pair
+// up (n_pad a multiple of 256) and the group's pairs fit on the grid at once.  Pairs
+// are an option (NMFA_BATCH_PAIR128), not the default: measured on GB300 (SK n = 2000,
+// 1024 replicas) they run 10.43 against 9.71 ms per run, because the MMA phase is
+// paced by MMA instruction issue (about 100 clocks per instruction under the epilogue
+// warps' noise draws, whether the instruction covers 128 or 256 rows), not by the
+// operand bytes the pair halves.  Results do not depend on it.
+bool tc_use_pair(int bn, int32_t n_pad) {
+  if (bn != 128 || n_pad % (2 * kBM) != 0) return false;
+  int clusters = 0;
+  if (co_resident_units(128, true, &clusters) != NMFA_OK) {
+    cudaGetLastError();
+    return false;
+  }
+  return n_pad / (2 * kBM) <= clusters;
+}
+
 // ---------------------------------------------------------------------------
 // Planning: every job (instance run) is split into groups of bn replicas; every
 // group needs nb = n_pad/128 co-resident CTAs for its whole run.  Groups are placed
@@ -906,18 +1052,22 @@ int tc_pick_bn(int32_t replicas, int32_t n_pad) {
 // ---------------------------------------------------------------------------
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
-  int capacity = 0;  // tile pipelines of the co-resident grid
-  int rc = co_resident_slots(jobs[0].bn, &capacity);
+  int capacity = 0;  // tile pipelines (or CTA pairs) of the co-resident grid
+  const bool pair = jobs[0].pair;
+  int rc = co_resident_slots(jobs[0].bn, pair, &capacity);
   if (rc) return rc;
   size_t ngroups = 0, nitems = 0, flags = 0, state = 0;
   for (int j = 0; j < count; ++j) {
     const int bn = jobs[j].bn;
     const int nb = jobs[j].pb.n_pad / kBM;
-    if (bn != jobs[0].bn) return set_error(NMFA_EINVAL, "one plan takes one tile width");
-    if (nb > capacity) return set_error(NMFA_EUNSUPPORTED, "tensor path: n too large for one co-resident replica block");
+    if (bn != jobs[0].bn || jobs[j].pair != pair) return set_error(NMFA_EINVAL, "one plan takes one tile variant");
+    if (pair && nb % 2 != 0) return set_error(NMFA_EINVAL, "CTA pairs need an even number of row blocks");
+    const int units = pair ? nb / 2 : nb;
+    if (units > capacity)
+      return set_error(NMFA_EUNSUPPORTED, "tensor path: n too large for one co-resident replica block");
     const int groups = (jobs[j].rp.replicas + bn - 1) / bn;
     ngroups += groups;
-    nitems += static_cast<size_t>(groups) * nb;
+    nitems += static_cast<size_t>(groups) * units;
     flags += static_cast<size_t>(groups) * nb;
     state += static_cast<size_t>(groups) * 2 * bn * jobs[j].pb.n_pad * 2;
   }
@@ -932,11 +1082,12 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,
                   bool withhold_tile) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
-  int ctas = 0;
-  int rc = co_resident_ctas(jobs[0].bn, &ctas);
+  const bool pair = jobs[0].pair;
+  int ctas = 0;  // scheduling units: CTAs, or CTA pairs
+  int rc = co_resident_units(jobs[0].bn, pair, &ctas);
   if (rc) return rc;
-  const int subs = tc_subs(jobs[0].bn);
-  // scheduler slot s is pipeline s / ctas of CTA s % ctas: every CTA's first
+  const int subs = tc_subs(jobs[0].bn, pair);
+  // scheduler slot s is pipeline s / ctas of unit s % ctas: every unit's first
   // pipeline fills before any second one
   const int capacity = ctas * subs;
   int64_t need = 0;
@@ -950,11 +1101,12 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   size_t nitems = 0, nflags = 0;
   for (int j = 0; j < count; ++j) {
     const int bn = jobs[j].bn, nb = jobs[j].pb.n_pad / kBM;
+    const int units = pair ? nb / 2 : nb;  // work items (tiles, or pairs of tiles) of a group
     const int groups = (jobs[j].rp.replicas + bn - 1) / bn;
     const int steps = jobs[j].rp.t_f + (tc_fuses_energy(jobs[j].pb, jobs[j].rp) ? 1 : 0);
     for (int c = 0; c < groups; ++c) {
-      gl.push_back({j, c, nb, static_cast<double>(steps) * (2.0 * nb + 8.0)});
-      nitems += nb;
+      gl.push_back({j, c, units, static_cast<double>(steps) * (2.0 * nb + 8.0)});
+      nitems += units;
       nflags += nb;
     }
   }
@@ -994,7 +1146,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     g.seed_hi = static_cast<uint32_t>(jb.rp.seed >> 32);
     g.stream = jb.rp.stream_id;
     g.flags = reinterpret_cast<uint32_t*>(base + off_flags) + flag_pos;
-    flag_pos += gl[k].nb;
+    flag_pos += g.n_pad / kBM;
     g.energy_pass = tc_fuses_energy(jb.pb, jb.rp) ? 1 : 0;
     g.e_done = reinterpret_cast<uint32_t*>(base + off_done) + k;
     g.e2h = reinterpret_cast<int64_t*>(base + off_e2h) + k * static_cast<size_t>(bn);
@@ -1003,7 +1155,8 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     g.S16 = reinterpret_cast<__nv_bfloat16*>(base + state_pos);
     state_pos += static_cast<size_t>(2) * bn * g.n_pad * 2;
     if ((rc = make_map_bf16(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad, kBM))) return rc;
-    if ((rc = make_map_bf16(&g.tmS, g.S16, 2ull * bn, g.n_pad, bn))) return rc;
+    // a pair's CTAs each load half of the group's replicas of every S slice
+    if ((rc = make_map_bf16(&g.tmS, g.S16, 2ull * bn, g.n_pad, pair ? bn / 2 : bn))) return rc;
   }
   // list scheduling of groups onto CTA slots
   std::vector<int> order(gl.size());
@@ -1023,7 +1176,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
       free_at[slots[b]] = start + gl[gi].dur;
     }
   }
-  int grid = 0;  // CTAs launched
+  int grid = 0;  // units launched (CTAs, or CTA pairs)
   for (int s = 0; s < capacity; ++s)
     if (!per_slot[s].empty()) grid = std::max(grid, s % ctas + 1);
   // the kernel's work lists in its order: pipeline-major, sub * grid + cta
@@ -1042,8 +1195,9 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   plan->first_off = off_first;
   plan->flags_off = off_flags;
   plan->flags_bytes = off_state - off_flags;  // flags, done counters and 2H sums
-  plan->grid = grid;
+  plan->grid = pair ? 2 * grid : grid;  // CTAs launched
   plan->bn = jobs[0].bn;
+  plan->pair = pair;
   plan->status = status;
   plan->makespan = *std::max_element(free_at.begin(), free_at.end());
   return NMFA_OK;
@@ -1077,24 +1231,33 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
     return rc;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.grid, 1, 1);
-  cfg.blockDim = dim3(plan.bn == 64    ? TcShape<64>::kThreads
+  cfg.blockDim = dim3(plan.pair        ? TcShape<128, true>::kThreads
+                      : plan.bn == 64  ? TcShape<64>::kThreads
                       : plan.bn == 256 ? TcShape<256>::kThreads
                                        : TcShape<128>::kThreads,
                       1, 1);
-  cfg.dynamicSmemBytes = plan.bn == 64    ? TcShape<64>::kSmemBytes
+  cfg.dynamicSmemBytes = plan.pair        ? TcShape<128, true>::kSmemBytes
+                         : plan.bn == 64  ? TcShape<64>::kSmemBytes
                          : plan.bn == 256 ? TcShape<256>::kSmemBytes
                                           : TcShape<128>::kSmemBytes;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  // cooperative: every CTA of the grid is resident at once (the tiles of a group wait
+  // for one another); CTA pairs are clusters of two
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 2;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = plan.pair ? 2 : 1;
   const char* d = static_cast<const char*>(plan.dev);
   const TcGroup* dg = reinterpret_cast<const TcGroup*>(d + plan.groups_off);
   const TcItem* di = reinterpret_cast<const TcItem*>(d + plan.items_off);
   const int32_t* df = reinterpret_cast<const int32_t*>(d + plan.first_off);
-  const cudaError_t ce = plan.bn == 64    ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
+  const cudaError_t ce = plan.pair        ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, true>, dg, di, df, plan.status)
+                         : plan.bn == 64  ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
                          : plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256>, dg, di, df, plan.status)
                                           : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128>, dg, di, df, plan.status);
   if ((rc = cuda_error(ce, "tensor kernel launch"))) return rc;

@@ -1087,15 +1087,19 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.rp.energy_i64 = jb.energy_i64_dev;
     b->energy_fused.push_back(tc_fuses_energy(t.pb, t.rp) ? 1 : 0);
     t.bn = (options & NMFA_BATCH_BN64) ? 64
-           : (options & NMFA_BATCH_BN128) ? 128
+           : (options & (NMFA_BATCH_BN128 | NMFA_BATCH_PAIR128)) ? 128
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
                                              : tc_pick_bn(jb.replicas, p->n_pad);
+    // CTA pairs only on request (where the problem allows them)
+    t.pair = (options & NMFA_BATCH_PAIR128) && tc_use_pair(t.bn, p->n_pad);
     b->bn.push_back(t.bn);
   }
-  for (int bnv : {256, 128, 64}) {
+  // one persistent launch per tile variant present in the batch
+  const std::pair<int, bool> variants[] = {{256, false}, {128, true}, {128, false}, {64, false}};
+  for (const auto& var : variants) {
     std::vector<TcJob> part;
     for (const TcJob& t : tj)
-      if (t.bn == bnv) part.push_back(t);
+      if (t.bn == var.first && t.pair == var.second) part.push_back(t);
     if (part.empty()) continue;
     int64_t bytes = 0;
     if ((rc = tc_plan_bytes(part.data(), static_cast<int32_t>(part.size()), &bytes))) return fail(rc);
@@ -1178,6 +1182,17 @@ int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t
 }
 
 void nmfa_batch_destroy(nmfa_batch* b) { free_batch(b); }
+
+int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t capacity, int32_t* count) {
+  if (b == nullptr) return set_error(NMFA_EINVAL, "NULL batch");
+  const int32_t n = static_cast<int32_t>(b->plans.size());
+  for (int32_t k = 0; k < n && k < capacity; ++k) {
+    if (bn) bn[k] = b->plans[k].bn;
+    if (ctas_per_mma) ctas_per_mma[k] = b->plans[k].pair ? 2 : 1;
+  }
+  if (count) *count = n;
+  return NMFA_OK;
+}
 
 // Tuning hook for the CUDA-core paths (replicas per CTA: 0 = automatic, else 1/2/4/8).
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {

@@ -145,18 +145,22 @@ struct TcJob {
   TcProblem pb;
   RunParams rp;
   int bn;                  // replicas per tile: 64, 128 or 256
+  bool pair = false;       // 128-replica tiles as CTA pairs (cta_group::2 MMAs of M = 256)
 };
 struct TcPlan {
   std::vector<unsigned char> host;   // group descriptors, items, per-CTA offsets
   void* dev = nullptr;               // workspace base
   size_t groups_off = 0, items_off = 0, first_off = 0, flags_off = 0, flags_bytes = 0;
-  int grid = 0;
+  int grid = 0;                      // CTAs launched
   int bn = 128;
+  bool pair = false;
   int32_t* status = nullptr;
   double makespan = 0.0;             // scheduler's estimate (relative units)
 };
 // Default replicas per tile (64, 128 or 256) of a run of `replicas` replicas of an n_pad problem.
 int tc_pick_bn(int32_t replicas, int32_t n_pad);
+// Whether 128-replica tiles of an n_pad problem run as CTA pairs (results do not change).
+bool tc_use_pair(int bn, int32_t n_pad);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
 // withhold_tile (test only): leave group 0's last row-block tile out of the work lists.
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,

@@ -92,9 +92,13 @@ struct nmfa_server {
 
 namespace {
 
+// Device memory a request holds while admitted: its couplings (stored and the BF16
+// expansion a run of FP8-stored J uses), the creation-time FP64 copy, the tensor
+// kernel's scratch and its inputs/outputs.  The state is counted for the widest tile
+// the library may pick (256 replicas), so admission never under-counts it.
 int64_t request_footprint(const Request* r) {
   const int64_t n = r->n, n_pad = (n + 127) / 128 * 128;
-  const int64_t bn = r->replicas <= 64 ? 64 : 128;
+  const int64_t bn = r->replicas <= 64 ? 64 : 256;
   const int64_t r_pad = (r->replicas + bn - 1) / bn * bn;
   const int64_t jq = (r->precision == NMFA_BF16 ? 2 : 1) * n_pad * n_pad;
   const int64_t creation = 8 * n * n;                      // FP64 staging copy held by the problem

@@ -46,6 +46,7 @@ SIGNATURES = {
     "nmfa_batch_sync": (ctypes.c_int, [_P]),
     "nmfa_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "nmfa_batch_destroy": (None, [_P]),
+    "nmfa_batch_plan": (ctypes.c_int, [_P, _P, _P, _i32, _P]),
     "nmfa_autotune_bn": (ctypes.c_int, [_P, _i32, _P]),
     "nmfa_server_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "nmfa_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(_u64)]),
@@ -225,6 +226,7 @@ NMFA_BATCH_GRAPH = 1
 NMFA_BATCH_AUTOTUNE = 2
 NMFA_BATCH_BN64 = 4
 NMFA_BATCH_BN128 = 16
+NMFA_BATCH_PAIR128 = 32
 NMFA_BATCH_DEBUG_WITHHOLD_TILE = 8
 
 
@@ -260,6 +262,13 @@ def nmfa_batch_info(batch):
 
 def nmfa_batch_destroy(batch):
     load().nmfa_batch_destroy(batch)
+
+
+def nmfa_batch_plan(batch):
+    """[(replicas per tile, CTAs per MMA)] for each persistent launch of the batch."""
+    bn, cp, cnt = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), ctypes.c_int32()
+    _check(load().nmfa_batch_plan(batch, bn, cp, 8, ctypes.byref(cnt)))
+    return [(bn[k], cp[k]) for k in range(min(cnt.value, 8))]
 
 
 def nmfa_autotune_bn(handle, replicas):

@@ -209,3 +209,35 @@ def test_256_replica_tiles_match_64_replica_tiles():
     for r in (0, 777, R - 1):
         assert e256[r] == oracle.energy_i64(J, s256[r])
     p.close()
+
+
+# --------------------------------------------------------------------------
+# CTA pairs (NMFA_BATCH_PAIR128): 128-replica tiles of problems whose row blocks pair
+# up run as clusters of two CTAs sharing one cta_group::2 MMA (M = 256).  Every tile
+# variant sweeps K in the same order, so the pairs' results are bit-identical to
+# one-CTA 128- and 64-replica tiles, and the energies exact against the oracle.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,R", [(256, 128), (1000, 384), (2000, 1024)])
+def test_cta_pairs_match_single_cta_tiles(n, R):
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(n, 70 + n)
+    p = nmfa.Problem(J, precision="bf16")
+    T = torch.as_tensor(inst.schedule(60), device=dev)
+    res = {}
+    for name, options, plan in (("pair", nmfa.NMFA_BATCH_PAIR128, [(128, 2)]), ("one", nmfa.NMFA_BATCH_BN128, [(128, 1)]),
+                                ("bn64", nmfa.NMFA_BATCH_BN64, [(64, 1)])):
+        b, outs = _batch([p], [(T, R, 8, 3)], options)
+        assert nmfa.nmfa_batch_plan(b) == plan, (name, nmfa.nmfa_batch_plan(b))
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        res[name] = (outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy())
+        nmfa.nmfa_batch_destroy(b)
+    for name in ("one", "bn64"):
+        np.testing.assert_array_equal(res["pair"][0], res[name][0])
+        np.testing.assert_array_equal(res["pair"][1], res[name][1])
+    s, e = _alone(p, T, R, 8, 3)  # the default pick: one CTA per tile
+    np.testing.assert_array_equal(s, res["pair"][0])
+    for r in (0, R // 2 + 1, R - 1):
+        assert res["pair"][1][r] == oracle.energy_i64(J, res["pair"][0][r])
+    p.close()
