@@ -242,10 +242,13 @@ int nmfa_batch_sync(nmfa_batch* b);
 int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes);
 void nmfa_batch_destroy(nmfa_batch* b);
 /* The batch's persistent launches (one per tile variant present): for launch k,
- * bn[k] = replicas per tile (64, 128 or 256) and ctas_per_mma[k] = 1, or 2 for CTA
- * pairs sharing one cta_group::2 MMA.  Writes at most `capacity` entries; *count
- * receives the number of launches.  Host arrays; any output may be NULL. */
-int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t capacity, int32_t* count);
+ * bn[k] = replicas per tile (64, 128 or 256), ctas_per_mma[k] = 1, or 2 for CTA
+ * pairs sharing one cta_group::2 MMA, and cluster_ctas[k] = CTAs per thread-block
+ * cluster (1, or 2 for pairs).
+ * Writes at most `capacity` entries; *count receives the number of launches.  Host
+ * arrays; any output may be NULL. */
+int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t* cluster_ctas,
+                    int32_t capacity, int32_t* count);
 
 /* Autotuner entry: the replicas-per-tile (64, 128 or 256) the tensor path would use for
  * `replicas` replicas of this problem, measured once per (n rounded to 128,
@@ -302,7 +305,10 @@ int nmfa_server_submit(nmfa_server* s, const nmfa_request* req, uint64_t* ticket
 int nmfa_server_poll(nmfa_server* s, uint64_t ticket, nmfa_result* out, int8_t* best_signs);
 /* Waits until every submitted request is done (NMFA_ETIMEOUT after timeout_s). */
 int nmfa_server_drain(nmfa_server* s, double timeout_s);
-int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding);
+/* Persistent launches so far, device memory held by admitted requests, requests not
+ * finished, and the most requests one launch has carried (any pointer may be NULL). */
+int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding,
+                      int32_t* max_requests_per_launch);
 /* Stops the loop (waits for launches on the GPU) and frees everything. */
 void nmfa_server_destroy(nmfa_server* s);
 

@@ -1183,12 +1183,14 @@ int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t
 
 void nmfa_batch_destroy(nmfa_batch* b) { free_batch(b); }
 
-int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t capacity, int32_t* count) {
+int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int32_t* cluster_ctas, int32_t capacity,
+                    int32_t* count) {
   if (b == nullptr) return set_error(NMFA_EINVAL, "NULL batch");
   const int32_t n = static_cast<int32_t>(b->plans.size());
   for (int32_t k = 0; k < n && k < capacity; ++k) {
     if (bn) bn[k] = b->plans[k].bn;
     if (ctas_per_mma) ctas_per_mma[k] = b->plans[k].pair ? 2 : 1;
+    if (cluster_ctas) cluster_ctas[k] = b->plans[k].pair ? 2 : 1;
   }
   if (count) *count = n;
   return NMFA_OK;

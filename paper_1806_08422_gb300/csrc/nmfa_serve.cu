@@ -84,6 +84,7 @@ struct nmfa_server {
   std::vector<cudaStream_t> streams;
   std::vector<bool> slot_busy;
   std::atomic<int64_t> launches{0};
+  int32_t max_batch = 0;          // most requests one launch has carried
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -235,6 +236,10 @@ int launch_batch(nmfa_server* s, std::vector<Request*>& reqs, int slot, InFlight
     r->res.spin_updates += static_cast<int64_t>(r->replicas) * r->n * r->t_f;
   }
   s->launches += 1;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->max_batch = std::max<int32_t>(s->max_batch, static_cast<int32_t>(reqs.size()));
+  }
   return NMFA_OK;
 }
 
@@ -410,9 +415,11 @@ int nmfa_server_drain(nmfa_server* s, double timeout_s) {
   return done ? NMFA_OK : set_error(NMFA_ETIMEOUT, "requests still outstanding");
 }
 
-int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding) {
+int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding,
+                      int32_t* max_requests_per_launch) {
   if (s == nullptr) return set_error(NMFA_EINVAL, "NULL server");
   std::lock_guard<std::mutex> g(s->mu);
+  if (max_requests_per_launch) *max_requests_per_launch = s->max_batch;
   if (launches) *launches = s->launches.load();
   if (mem_used) *mem_used = s->mem_used;
   if (outstanding) *outstanding = s->outstanding;

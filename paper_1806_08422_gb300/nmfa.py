@@ -46,13 +46,13 @@ SIGNATURES = {
     "nmfa_batch_sync": (ctypes.c_int, [_P]),
     "nmfa_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "nmfa_batch_destroy": (None, [_P]),
-    "nmfa_batch_plan": (ctypes.c_int, [_P, _P, _P, _i32, _P]),
+    "nmfa_batch_plan": (ctypes.c_int, [_P, _P, _P, _P, _i32, _P]),
     "nmfa_autotune_bn": (ctypes.c_int, [_P, _i32, _P]),
     "nmfa_server_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "nmfa_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(_u64)]),
     "nmfa_server_poll": (ctypes.c_int, [_P, _u64, _P, _P]),
     "nmfa_server_drain": (ctypes.c_int, [_P, _f64]),
-    "nmfa_server_stats": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nmfa_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nmfa_server_destroy": (None, [_P]),
     "nmfa_debug_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _i32, _P, _P, _P, _P, _P,
                                       _P, _P]),
@@ -265,10 +265,11 @@ def nmfa_batch_destroy(batch):
 
 
 def nmfa_batch_plan(batch):
-    """[(replicas per tile, CTAs per MMA)] for each persistent launch of the batch."""
-    bn, cp, cnt = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), ctypes.c_int32()
-    _check(load().nmfa_batch_plan(batch, bn, cp, 8, ctypes.byref(cnt)))
-    return [(bn[k], cp[k]) for k in range(min(cnt.value, 8))]
+    """[(replicas per tile, CTAs per MMA, CTAs per cluster)] for each persistent launch
+    of the batch."""
+    bn, cp, cc, cnt = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), ctypes.c_int32()
+    _check(load().nmfa_batch_plan(batch, bn, cp, cc, 8, ctypes.byref(cnt)))
+    return [(bn[k], cp[k], cc[k]) for k in range(min(cnt.value, 8))]
 
 
 def nmfa_autotune_bn(handle, replicas):
@@ -331,9 +332,9 @@ def nmfa_server_drain(server, timeout_s=600.0):
 
 
 def nmfa_server_stats(server):
-    la, mu, out = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
-    _check(load().nmfa_server_stats(server, ctypes.byref(la), ctypes.byref(mu), ctypes.byref(out)))
-    return {"launches": la.value, "mem_used": mu.value, "outstanding": out.value}
+    la, mu, out, mb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nmfa_server_stats(server, ctypes.byref(la), ctypes.byref(mu), ctypes.byref(out), ctypes.byref(mb)))
+    return {"launches": la.value, "mem_used": mu.value, "outstanding": out.value, "max_requests_per_launch": mb.value}
 
 
 def nmfa_server_destroy(server):

@@ -225,8 +225,8 @@ def test_cta_pairs_match_single_cta_tiles(n, R):
     p = nmfa.Problem(J, precision="bf16")
     T = torch.as_tensor(inst.schedule(60), device=dev)
     res = {}
-    for name, options, plan in (("pair", nmfa.NMFA_BATCH_PAIR128, [(128, 2)]), ("one", nmfa.NMFA_BATCH_BN128, [(128, 1)]),
-                                ("bn64", nmfa.NMFA_BATCH_BN64, [(64, 1)])):
+    for name, options, plan in (("pair", nmfa.NMFA_BATCH_PAIR128, [(128, 2, 2)]),
+                                ("one", nmfa.NMFA_BATCH_BN128, [(128, 1, 1)]), ("bn64", nmfa.NMFA_BATCH_BN64, [(64, 1, 1)])):
         b, outs = _batch([p], [(T, R, 8, 3)], options)
         assert nmfa.nmfa_batch_plan(b) == plan, (name, nmfa.nmfa_batch_plan(b))
         nmfa.nmfa_batch_launch(b)

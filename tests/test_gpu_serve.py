@@ -52,7 +52,9 @@ def test_server_results_equal_solo_runs():
             best = min(_solo_best(J, T, R, seed, a)[0] for a in range(3))
             assert res["best_energy"] == best
     st = nmfa.nmfa_server_stats(srv)
-    assert st["outstanding"] == 0 and st["launches"] >= 2
+    # nine runs in all (three requests once, two three times); whether two of them share
+    # a launch depends on arrival timing here (the test below shows it deterministically)
+    assert st["outstanding"] == 0 and 2 <= st["launches"] <= 9 and st["max_requests_per_launch"] >= 1, st
     nmfa.nmfa_server_destroy(srv)
 
 
@@ -72,4 +74,40 @@ def test_server_memory_budget_admits_in_order():
             break
         time.sleep(0.01)
     assert nmfa.nmfa_server_stats(srv)["mem_used"] == 0
+    nmfa.nmfa_server_destroy(srv)
+
+
+def test_request_arriving_mid_launch_starts_before_that_launch_ends():
+    # Continuous batching: a long request A is on the GPU when B arrives; B starts in a
+    # second launch on the SMs A leaves free, before A's launch has ended, and its
+    # result is that of B run alone.  Requests batched behind a busy slot share a launch.
+    import time
+    from paper_1806_08422_gb300 import nmfa
+    JA, JB = inst.sk(1000, 11), inst.sk(200, 12)
+    TA, TB = inst.schedule(20000), inst.schedule(150)
+    srv = nmfa.nmfa_server_create(0, 2, 1)
+    ta = nmfa.nmfa_server_submit(srv, JA, TA, 128, 1e18, seed=3)
+    for _ in range(2000):  # until A's launch is on the GPU
+        if nmfa.nmfa_server_poll(srv, ta)["state"] == 2:
+            break
+        time.sleep(0.001)
+    assert nmfa.nmfa_server_poll(srv, ta)["state"] == 2
+    tb = nmfa.nmfa_server_submit(srv, JB, TB, 64, 1e18, seed=4)
+    nmfa.nmfa_server_drain(srv, 300.0)
+    ra, rb = nmfa.nmfa_server_poll(srv, ta), nmfa.nmfa_server_poll(srv, tb, n=200)
+    assert ra["state"] == 3 and rb["state"] == 3 and ra["error"] == 0 and rb["error"] == 0
+    assert rb["t_submit"] > ra["t_first_start"]
+    assert rb["t_first_start"] < ra["t_done"], (rb["t_first_start"], ra["t_done"])
+    e, s = _solo_best(JB, TB, 64, 4, 0)
+    assert rb["best_energy"] == e
+    np.testing.assert_array_equal(rb["best_signs"], s)
+    nmfa.nmfa_server_destroy(srv)
+    # one launch slot: requests that arrive while it is busy share the next launch
+    srv = nmfa.nmfa_server_create(0, 1, 1)
+    ts = [nmfa.nmfa_server_submit(srv, JA, inst.schedule(3000), 64, 1e18, seed=5)]
+    ts += [nmfa.nmfa_server_submit(srv, inst.sk(150, 20 + k), TB, 64, 1e18, seed=6 + k) for k in range(4)]
+    nmfa.nmfa_server_drain(srv, 300.0)
+    assert all(nmfa.nmfa_server_poll(srv, t)["state"] == 3 for t in ts)
+    st = nmfa.nmfa_server_stats(srv)
+    assert st["launches"] < 5 and st["max_requests_per_launch"] >= 2, st
     nmfa.nmfa_server_destroy(srv)
