@@ -857,41 +857,6 @@ __global__ void convert_vec_kernel(int n, const double* __restrict__ src, void* 
   if (i < n) store_kind(dst, i, src != nullptr ? src[i] : 0.0, kind);
 }
 
-// E4M3 -> BF16 expansion of a stored coupling matrix (every stored value is an
-// exact E4M3 number; BF16 holds every such value exactly), 16 values per thread.
-__global__ void expand_e4m3_bf16_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n16;
-       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint4 w = src[k];
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    uint32_t out[8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const __nv_fp8_storage_t lo = static_cast<__nv_fp8_storage_t>((words[q] >> (16 * h)) & 0xFF);
-        const __nv_fp8_storage_t hi = static_cast<__nv_fp8_storage_t>((words[q] >> (16 * h + 8)) & 0xFF);
-        const float flo = __half2float(__half(__nv_cvt_fp8_to_halfraw(lo, __NV_E4M3)));
-        const float fhi = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
-        const __nv_bfloat162 pr = __floats2bfloat162_rn(flo, fhi);
-        out[2 * q + h] = *reinterpret_cast<const uint32_t*>(&pr);
-      }
-    }
-    dst[2 * k] = make_uint4(out[0], out[1], out[2], out[3]);
-    dst[2 * k + 1] = make_uint4(out[4], out[5], out[6], out[7]);
-  }
-}
-
-int launch_expand_e4m3_bf16(const void* src, void* dst, int64_t count, cudaStream_t st) {
-  if (count % 16 != 0) return set_error(NMFA_EINVAL, "E4M3 expansion needs a multiple of 16 values");
-  const int64_t n16 = count / 16;
-  const int grid = static_cast<int>(std::min<int64_t>((n16 + 255) / 256, 4096));
-  expand_e4m3_bf16_kernel<<<std::max(grid, 1), 256, 0, st>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst),
-                                                             n16);
-  count_launch();
-  return cuda_error(cudaGetLastError(), "E4M3 expansion launch");
-}
-
 int launch_row_norms_dense(int32_t n, const double* J64, const double* h, double* d, float* inv_d32,
                            cudaStream_t st) {
   row_norms_dense_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, J64, h, d, inv_d32);

@@ -94,13 +94,19 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   lands 48 KB of operands per 128-deep K slice instead of 64 KB, and the tensor
 //   core reads 96 instead of 128 bytes per clock from each SM's shared memory (at
 //   the full MMA rate).  Ring of 4 slots of 48 KB; the even CTA issues the MMAs.
-template <int BN, bool PAIR = false>
+//   FP8 (F8 = true, 128 or 256 replicas, one CTA per tile): J is stored in E4M3; its
+//   slices go by TMA into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes)
+//   and two converter warps write them as BF16 into the slot's A operand (the MMA
+//   stays kind::f16 with both operands BF16); the slot's full barrier then also
+//   waits for both converter warps.
+template <int BN, bool PAIR = false, bool F8 = false>
 struct TcShape {
   static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
   static constexpr int kColsPerWarp = BN == 256 ? 64 : 32;
   static constexpr int kEpiWarps = BN == 256 ? 16 : BN / 8;
   static constexpr int kSubs = (BN == 64 && !PAIR) ? 2 : 1;  // tile pipelines per CTA
-  static constexpr int kSubWarps = 2 + kEpiWarps;  // warps per pipeline
+  static constexpr int kConvWarps = F8 ? 2 : 0;                 // FP8 -> BF16 converter warps
+  static constexpr int kSubWarps = 2 + kEpiWarps + kConvWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
   static constexpr int kBRows = PAIR ? BN / 2 : BN;  // replica rows of each B slice in this CTA
   static constexpr int kStages = PAIR ? 4 : (BN == 128 ? 3 : 2);  // ring slots per pipeline
@@ -108,7 +114,10 @@ struct TcShape {
   static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
   static constexpr int kMmaM = PAIR ? 2 * kBM : kBM;
   static constexpr uint32_t kRingBytes = kStages * kStageBytes;
-  static constexpr size_t kSmemBytes = static_cast<size_t>(kSubs) * kRingBytes + 1024;
+  static constexpr uint32_t kStgBytes = kBM * kKSlot;  // one E4M3 slice: 128 rows x 128 K bytes
+  static constexpr int kStgStages = 2;
+  static constexpr size_t kSmemBytes =
+      static_cast<size_t>(kSubs) * kRingBytes + (F8 ? kStgStages * kStgBytes : 0u) + 1024;
   static constexpr uint32_t kTmemCols = 512;  // allocated once per CTA
   static constexpr uint32_t kSubCols = kTmemCols / kSubs;
   static constexpr uint32_t kColAcc1 = kDoubleAcc ? BN : 0;
@@ -118,6 +127,7 @@ struct TcShape {
   static_assert(kEpiWarps * kColsPerWarp == 4 * BN, "every (quarter, column) pair once");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
   static_assert(!PAIR || BN == 128, "CTA pairs take 128-replica tiles");
+  static_assert(!F8 || (!PAIR && BN != 64), "FP8 couplings take one-CTA 128- or 256-replica tiles");
 };
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A pipeline that reaches a new group early waits for the group's other pipelines to
@@ -172,6 +182,9 @@ struct SharedCtl {
   // epilogue warps arrive from the other CTA), so each CTA copies the pair's other
   // row block without a round trip through that block's epoch counter.
   uint64_t pair_pub;
+  // FP8: staged E4M3 slice landed (TMA) / consumed by both converter warps
+  uint64_t stg_full[2];
+  uint64_t stg_empty[2];
   uint64_t drain;
   uint32_t tmem_slot;
   int32_t abort_flag;
@@ -567,11 +580,11 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
 // its pair-aligned row block (b & ~1) and wrapping; the two tiles of a CTA pair share
 // one MMA and therefore one order, and every tile variant uses the same rule, so the
 // FP32 sums of every output (and with them the results) do not depend on the variant.
-template <int BN, int SUB, bool PAIR>
+template <int BN, int SUB, bool PAIR, bool F8>
 __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items,
                                              const int32_t* __restrict__ first, int32_t* status, SharedCtl* ctl_all,
                                              uint32_t ring_base, uint32_t tmem_base, int warp, int lane) {
-  using Shape = TcShape<BN, PAIR>;
+  using Shape = TcShape<BN, PAIR, F8>;
   constexpr int kEpiWarps = Shape::kEpiWarps;
   constexpr int kSubWarps = Shape::kSubWarps;
   constexpr int kStages = Shape::kStages;
@@ -585,6 +598,8 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
   const int w_begin = first[slot], w_end = first[slot + 1];
   const uint32_t ring = ring_base + static_cast<uint32_t>(SUB) * Shape::kRingBytes;
   const uint32_t tmem = tmem_base + static_cast<uint32_t>(SUB) * Shape::kSubCols;
+  // FP8 staging ring (after the operand ring; 1024-aligned like it)
+  const uint32_t stg_base = ring_base + static_cast<uint32_t>(Shape::kSubs) * Shape::kRingBytes;
 
   if (lw == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -609,6 +624,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       else
         ptx::tma_load_2d_warp(dst, tm, x, y, full0 + 8u * st);
     };
+    const uint32_t stg_full0 = ptx::smem_u32(&ctl.stg_full[0]), stg_empty0 = ptx::smem_u32(&ctl.stg_empty[0]);
     for (int w = w_begin; w < w_end && ok; ++w) {
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
@@ -617,9 +633,25 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       const void* tmJ = &g->tmJ;
       const void* tmS = &g->tmS;
       const uint32_t* gflags = g->flags;
-      // bytes that complete one slot's full barrier: both CTAs' copies for a pair
+      // bytes that complete one slot's full barrier: both CTAs' copies for a pair; for
+      // FP8 only the S copies (the converter warps write the J operand and arrive)
       const uint32_t stage_tx = (PAIR ? 2u : 1u) * kAtoms *
-                                (kABytes + static_cast<uint32_t>(PAIR ? bn / 2 : bn) * 128u);
+                                ((F8 ? 0u : kABytes) + static_cast<uint32_t>(PAIR ? bn / 2 : bn) * 128u);
+      // the J slice of fill `fill` into ring slot `st`: BF16 straight into the slot, or
+      // (FP8) the E4M3 slice into the staging buffer the converter warps read
+      auto load_j = [&](int ks, uint32_t st, uint32_t fill) -> bool {
+        if constexpr (F8) {
+          const uint32_t jb = fill & 1u;
+          if (!__all_sync(0xffffffffu, wait_bar(stg_empty0 + 8u * jb, ((fill >> 1) & 1u) ^ 1u, &ctl, status)))
+            return false;
+          ptx::mbar_arrive_expect_tx_warp(stg_full0 + 8u * jb, Shape::kStgBytes);
+          ptx::tma_load_2d_warp(stg_base + jb * Shape::kStgBytes, tmJ, ks * kKSlot, b * kBM, stg_full0 + 8u * jb);
+        } else {
+#pragma unroll
+          for (int a = 0; a < kAtoms; ++a) load(ring + st * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, st);
+        }
+        return true;
+      };
       const int brow = PAIR ? static_cast<int>(crank) * (bn / 2) : 0;  // this CTA's replica rows of S
       const int KB = n_pad / kKSlot;  // ring slots per step (= row blocks)
       const int kslice_base = (b & ~1) % KB;
@@ -640,8 +672,8 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
           if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-#pragma unroll
-          for (int a = 0; a < kAtoms; ++a) load(ring + stage * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, stage);
+          ok = load_j(ks, stage, filled);
+          if (!ok) break;
           ++claimed;
           ++filled;
           if (++stage == kStages) {
@@ -687,9 +719,8 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
           if (!ok) break;
           const uint32_t sA = ring + stage * kStageBytes;
           if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-#pragma unroll
-          for (int a = 0; a < kAtoms; ++a) load(sA + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, stage);
-          ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
+          ok = load_j(ks, stage, filled);
+          if (ok) ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
 #pragma unroll
           for (int a = 0; a < kAtoms; ++a)
             load(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy, stage);
@@ -709,6 +740,14 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       // landed.  A pair's copies complete on the even CTA's full barriers, so the odd
       // CTA waits for its own slots to be released by the MMA commits instead.
       const uint32_t last = filled;
+      if constexpr (F8) {
+        // the staged E4M3 copies of the last fills (their barriers complete on landing)
+        for (uint32_t k = (last > 2u ? last - 2u : 0u); k < last; ++k) {
+          const uint64_t t0 = ptx::globaltimer_ns();
+          while (!ptx::mbar_try_wait(stg_full0 + 8u * (k & 1u), (k >> 1) & 1u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
+          }
+        }
+      }
       for (uint32_t k = (last > static_cast<uint32_t>(kStages) ? last - kStages : 0u); k < last; ++k) {
         const uint32_t st = k % kStages, ph = (k / kStages) & 1u;
         const uint64_t t0 = ptx::globaltimer_ns();
@@ -797,6 +836,71 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       while (!ptx::mbar_try_wait(ptx::smem_u32(&ctl.drain), 0u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
       }
     }
+  } else if (F8 && lw >= 2 + kEpiWarps) {
+    // ------------------------------------------------------------ FP8 converters
+    // Both warps walk the producer's fill sequence.  Fill f's E4M3 slice (128 rows of
+    // 128 bytes, 128-byte swizzle) becomes the BF16 A operand of ring slot f % kStages
+    // (two 128-byte-swizzle atoms of 64 K values): each thread takes 16-byte chunks,
+    // converts its 16 values and writes two 16-byte BF16 chunks.  The slot is free: the
+    // producer issued this fill's staging copy only after the slot's empty barrier.
+    const int ct = (lw - 2 - kEpiWarps) * 32 + lane;  // 0 .. 63
+    const uint32_t full0 = ptx::smem_u32(&ctl.full[0]);
+    const uint32_t stg_full0 = ptx::smem_u32(&ctl.stg_full[0]), stg_empty0 = ptx::smem_u32(&ctl.stg_empty[0]);
+    uint32_t fill = 0;
+    bool ok = true;
+    for (int w = w_begin; w < w_end && ok; ++w) {
+      const TcGroup* g = groups + items[w].group;
+      const int KB = g->n_pad / kKSlot, steps = g->t_f + g->energy_pass;
+      for (int t = 0; t < steps && ok; ++t) {
+        for (int kb = 0; kb < KB; ++kb, ++fill) {
+          const uint32_t jb = fill & 1u, st = fill % kStages;
+          ok = __all_sync(0xffffffffu, wait_bar(stg_full0 + 8u * jb, (fill >> 1) & 1u, &ctl, status));
+          if (!ok) break;
+          const uint32_t src = stg_base + jb * Shape::kStgBytes;
+          const uint32_t dst = ring + st * kStageBytes;
+          // four chunks per round: their loads, then their conversions, then their
+          // stores, so that each thread has independent work in flight
+          constexpr int kChunks = (kBM * kKSlot / 16) / 64;  // 16 per thread
+#pragma unroll 1
+          for (int it0 = 0; it0 < kChunks; it0 += 4) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = ct + 64 * (it0 + u);  // 16-byte chunk of the slice
+              const int r = q >> 3, c = q & 7;     // row, K values 16c .. 16c + 15
+              v[u] = ptx::ld_shared_v4(src + static_cast<uint32_t>(r) * 128u +
+                                       ((static_cast<uint32_t>(c) ^ static_cast<uint32_t>(r & 7)) << 4));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = ct + 64 * (it0 + u);
+              const int r = q >> 3, c = q & 7;
+              const uint32_t sw = static_cast<uint32_t>(r & 7);
+              uint4 lo, hi;  // BF16 values 16c .. 16c+7 and 16c+8 .. 16c+15
+              lo.x = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].x));
+              lo.y = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].x >> 16));
+              lo.z = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].y));
+              lo.w = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].y >> 16));
+              hi.x = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].z));
+              hi.y = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].z >> 16));
+              hi.z = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].w));
+              hi.w = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].w >> 16));
+              // atom c / 4 holds K 64 (c / 4) .. +63; chunks 2 (c % 4) and the next of row r
+              const uint32_t atom = dst + static_cast<uint32_t>(c >> 2) * kABytes + static_cast<uint32_t>(r) * 128u;
+              const uint32_t c0 = static_cast<uint32_t>(2 * (c & 3));
+              ptx::st_shared_v4(atom + ((c0 ^ sw) << 4), lo);
+              ptx::st_shared_v4(atom + (((c0 + 1u) ^ sw) << 4), hi);
+            }
+          }
+          ptx::fence_proxy_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::mbar_arrive(stg_empty0 + 8u * jb);
+            ptx::mbar_arrive(full0 + 8u * st);
+          }
+        }
+      }
+    }
   } else {
     // ------------------------------------------------------------ epilogue
     // epilogue warp e (physical warp e + 2 + SUB * kSubWarps) serves column group
@@ -814,11 +918,11 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
   }
 }
 
-template <int BN, bool PAIR = false>
-__global__ void __launch_bounds__(TcShape<BN, PAIR>::kThreads, 1)
+template <int BN, bool PAIR = false, bool F8 = false>
+__global__ void __launch_bounds__(TcShape<BN, PAIR, F8>::kThreads, 1)
 nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items, const int32_t* __restrict__ first,
                int32_t* status) {
-  using Shape = TcShape<BN, PAIR>;
+  using Shape = TcShape<BN, PAIR, F8>;
   constexpr int kEpiWarps = Shape::kEpiWarps;
   constexpr int kSubs = Shape::kSubs, kSubWarps = Shape::kSubWarps;
   constexpr int kStages = Shape::kStages;
@@ -833,8 +937,13 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
     for (int p = 0; p < kSubs; ++p) {
       SharedCtl& c = ctl_all[p];
       for (int s = 0; s < kStages; ++s) {
-        ptx::mbar_init(ptx::smem_u32(&c.full[s]), 1);
+        // FP8: the producer's arrival (S bytes) and one arrival per converter warp
+        ptx::mbar_init(ptx::smem_u32(&c.full[s]), 1 + Shape::kConvWarps);
         ptx::mbar_init(ptx::smem_u32(&c.empty[s]), 1);
+      }
+      for (int j = 0; j < 2; ++j) {
+        ptx::mbar_init(ptx::smem_u32(&c.stg_full[j]), 1);
+        ptx::mbar_init(ptx::smem_u32(&c.stg_empty[j]), Shape::kConvWarps > 0 ? Shape::kConvWarps : 1);
       }
       ptx::mbar_init(ptx::smem_u32(&c.acc_full), 1);
       // a pair's MMA issuer waits for the bias of both CTAs' epilogue warps
@@ -865,12 +974,12 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
   const uint32_t tmem_base = ctl_all[0].tmem_slot;
 
   if constexpr (kSubs == 1) {
-    run_pipeline<BN, 0, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+    run_pipeline<BN, 0, PAIR, F8>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
   } else {
     if (warp < kSubWarps)
-      run_pipeline<BN, 0, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+      run_pipeline<BN, 0, PAIR, F8>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
     else
-      run_pipeline<BN, 1, PAIR>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
+      run_pipeline<BN, 1, PAIR, F8>(groups, items, first, status, ctl_all, ring_base, tmem_base, warp, lane);
   }
 
   ptx::tc_fence_before();
@@ -932,13 +1041,29 @@ int make_map_bf16(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols
 
 // Co-resident scheduling units of the persistent grid for one tile variant: CTAs
 // (one per SM), or for CTA pairs the clusters of two that fit at once.
-template <int BN, bool PAIR>
+// 2-D E4M3 (one byte per value) tensor map over a row-major [rows][cols] array, box =
+// 128 rows x 128 bytes with the 128-byte swizzle (the converter warps' staging layout).
+int make_map_u8(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols) {
+  auto enc = get_encode_fn();
+  if (enc == nullptr) return set_error(NMFA_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kKSlot), static_cast<cuuint32_t>(kBM)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(NMFA_ECUDA, "cuTensorMapEncodeTiled (E4M3) failed (" + std::to_string(r) + ")");
+  return NMFA_OK;
+}
+
+template <int BN, bool PAIR, bool F8>
 int co_resident_units_t(int* capacity) {
   static int cached = -1;
   if (cached < 0) {
-    using Shape = TcShape<BN, PAIR>;
+    using Shape = TcShape<BN, PAIR, F8>;
     int rc;
-    if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((rc = cuda_error(cudaFuncSetAttribute(nmfa_tc_kernel<BN, PAIR, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(Shape::kSmemBytes)),
                          "tensor kernel attribute")))
       return rc;
@@ -958,12 +1083,12 @@ int co_resident_units_t(int* capacity) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int clusters = 0;
-      if ((rc = cuda_error(cudaOccupancyMaxActiveClusters(&clusters, nmfa_tc_kernel<BN, PAIR>, &cfg),
+      if ((rc = cuda_error(cudaOccupancyMaxActiveClusters(&clusters, nmfa_tc_kernel<BN, PAIR, F8>, &cfg),
                            "cluster occupancy")))
         return rc;
       cached = std::min(clusters, sms / 2);
     } else {
-      if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN, PAIR>,
+      if ((rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmfa_tc_kernel<BN, PAIR, F8>,
                                                                          Shape::kThreads, Shape::kSmemBytes),
                            "occupancy")))
         return rc;
@@ -975,17 +1100,19 @@ int co_resident_units_t(int* capacity) {
   *capacity = cached;
   return NMFA_OK;
 }
-int co_resident_units(int bn, bool pair, int* capacity) {
-  if (pair) return co_resident_units_t<128, true>(capacity);
-  return bn == 64 ? co_resident_units_t<64, false>(capacity)
-                  : bn == 256 ? co_resident_units_t<256, false>(capacity) : co_resident_units_t<128, false>(capacity);
+int co_resident_units(int bn, bool pair, bool f8, int* capacity) {
+  if (pair) return co_resident_units_t<128, true, false>(capacity);
+  if (f8) return bn == 256 ? co_resident_units_t<256, false, true>(capacity) : co_resident_units_t<128, false, true>(capacity);
+  return bn == 64 ? co_resident_units_t<64, false, false>(capacity)
+                  : bn == 256 ? co_resident_units_t<256, false, false>(capacity)
+                              : co_resident_units_t<128, false, false>(capacity);
 }
 // Tile pipelines per scheduling unit.
 int tc_subs(int bn, bool pair) { return (bn == 64 && !pair) ? TcShape<64>::kSubs : 1; }
 // Work-list slots of the co-resident grid: tile pipelines, or CTA pairs.
-int co_resident_slots(int bn, bool pair, int* slots) {
+int co_resident_slots(int bn, bool pair, bool f8, int* slots) {
   int units = 0;
-  const int rc = co_resident_units(bn, pair, &units);
+  const int rc = co_resident_units(bn, pair, f8, &units);
   if (rc) return rc;
   *slots = units * tc_subs(bn, pair);
   return NMFA_OK;
@@ -1035,7 +1162,7 @@ int tc_pick_bn(int32_t replicas, int32_t n_pad) {
 bool tc_use_pair(int bn, int32_t n_pad) {
   if (bn != 128 || n_pad % (2 * kBM) != 0) return false;
   int clusters = 0;
-  if (co_resident_units(128, true, &clusters) != NMFA_OK) {
+  if (co_resident_units(128, true, false, &clusters) != NMFA_OK) {
     cudaGetLastError();
     return false;
   }
@@ -1053,14 +1180,16 @@ bool tc_use_pair(int bn, int32_t n_pad) {
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
   int capacity = 0;  // tile pipelines (or CTA pairs) of the co-resident grid
-  const bool pair = jobs[0].pair;
-  int rc = co_resident_slots(jobs[0].bn, pair, &capacity);
+  const bool pair = jobs[0].pair, f8 = jobs[0].pb.fp8;
+  int rc = co_resident_slots(jobs[0].bn, pair, f8, &capacity);
   if (rc) return rc;
   size_t ngroups = 0, nitems = 0, flags = 0, state = 0;
   for (int j = 0; j < count; ++j) {
     const int bn = jobs[j].bn;
     const int nb = jobs[j].pb.n_pad / kBM;
-    if (bn != jobs[0].bn || jobs[j].pair != pair) return set_error(NMFA_EINVAL, "one plan takes one tile variant");
+    if (bn != jobs[0].bn || jobs[j].pair != pair || jobs[j].pb.fp8 != f8)
+      return set_error(NMFA_EINVAL, "one plan takes one tile variant");
+    if (f8 && (pair || bn == 64)) return set_error(NMFA_EINVAL, "FP8 couplings take one-CTA 128- or 256-replica tiles");
     if (pair && nb % 2 != 0) return set_error(NMFA_EINVAL, "CTA pairs need an even number of row blocks");
     const int units = pair ? nb / 2 : nb;
     if (units > capacity)
@@ -1082,9 +1211,9 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,
                   bool withhold_tile) {
   if (count < 1) return set_error(NMFA_EINVAL, "empty plan");
-  const bool pair = jobs[0].pair;
+  const bool pair = jobs[0].pair, f8 = jobs[0].pb.fp8;
   int ctas = 0;  // scheduling units: CTAs, or CTA pairs
-  int rc = co_resident_units(jobs[0].bn, pair, &ctas);
+  int rc = co_resident_units(jobs[0].bn, pair, f8, &ctas);
   if (rc) return rc;
   const int subs = tc_subs(jobs[0].bn, pair);
   // scheduler slot s is pipeline s / ctas of unit s % ctas: every unit's first
@@ -1154,7 +1283,8 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
     g.energy_i64 = g.energy_pass ? jb.rp.energy_i64 : nullptr;
     g.S16 = reinterpret_cast<__nv_bfloat16*>(base + state_pos);
     state_pos += static_cast<size_t>(2) * bn * g.n_pad * 2;
-    if ((rc = make_map_bf16(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad, kBM))) return rc;
+    if ((rc = f8 ? make_map_u8(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad) : make_map_bf16(&g.tmJ, jb.pb.Jq, g.n_pad, g.n_pad, kBM)))
+      return rc;
     // a pair's CTAs each load half of the group's replicas of every S slice
     if ((rc = make_map_bf16(&g.tmS, g.S16, 2ull * bn, g.n_pad, pair ? bn / 2 : bn))) return rc;
   }
@@ -1198,6 +1328,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   plan->grid = pair ? 2 * grid : grid;  // CTAs launched
   plan->bn = jobs[0].bn;
   plan->pair = pair;
+  plan->f8 = f8;
   plan->status = status;
   plan->makespan = *std::max_element(free_at.begin(), free_at.end());
   return NMFA_OK;
@@ -1231,12 +1362,15 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
     return rc;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.grid, 1, 1);
-  cfg.blockDim = dim3(plan.pair        ? TcShape<128, true>::kThreads
+  cfg.blockDim = dim3(plan.f8 ? (plan.bn == 256 ? TcShape<256, false, true>::kThreads : TcShape<128, false, true>::kThreads)
+                      : plan.pair      ? TcShape<128, true>::kThreads
                       : plan.bn == 64  ? TcShape<64>::kThreads
                       : plan.bn == 256 ? TcShape<256>::kThreads
                                        : TcShape<128>::kThreads,
                       1, 1);
-  cfg.dynamicSmemBytes = plan.pair        ? TcShape<128, true>::kSmemBytes
+  cfg.dynamicSmemBytes = plan.f8 ? (plan.bn == 256 ? TcShape<256, false, true>::kSmemBytes
+                                                   : TcShape<128, false, true>::kSmemBytes)
+                         : plan.pair      ? TcShape<128, true>::kSmemBytes
                          : plan.bn == 64  ? TcShape<64>::kSmemBytes
                          : plan.bn == 256 ? TcShape<256>::kSmemBytes
                                           : TcShape<128>::kSmemBytes;
@@ -1256,7 +1390,11 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   const TcGroup* dg = reinterpret_cast<const TcGroup*>(d + plan.groups_off);
   const TcItem* di = reinterpret_cast<const TcItem*>(d + plan.items_off);
   const int32_t* df = reinterpret_cast<const int32_t*>(d + plan.first_off);
-  const cudaError_t ce = plan.pair        ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, true>, dg, di, df, plan.status)
+  const cudaError_t ce = plan.f8 ? (plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256, false, true>, dg, di, df,
+                                                                      plan.status)
+                                                   : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, false, true>, dg, di, df,
+                                                                      plan.status))
+                         : plan.pair      ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, true>, dg, di, df, plan.status)
                          : plan.bn == 64  ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
                          : plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256>, dg, di, df, plan.status)
                                           : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128>, dg, di, df, plan.status);
@@ -1265,21 +1403,28 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   return NMFA_OK;
 }
 
+// FP8-stored couplings take one-CTA 128- or 256-replica tiles (two converter warps
+// beside a pipeline's 18; the 64-replica CTA's two pipelines leave no room).  Results
+// do not depend on the width.
+int tc_pick_bn_for(const TcProblem& pb, int32_t replicas) {
+  const int bn = tc_pick_bn(replicas, pb.n_pad);
+  return (pb.fp8 && bn == 64) ? 128 : bn;
+}
+
 int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes) {
   TcJob jb{};
   jb.pb = pb;
   jb.rp.replicas = replicas;
-  jb.bn = tc_pick_bn(replicas, pb.n_pad);
+  jb.bn = tc_pick_bn_for(pb, replicas);
   return tc_plan_bytes(&jb, 1, bytes);
 }
 
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws, cudaStream_t st) {
-  if (pb.fp8) return set_error(NMFA_EINVAL, "tensor kernel takes BF16 couplings (expand FP8 storage first)");
   if (pb.n_pad % kBM != 0) return set_error(NMFA_EINVAL, "tensor path: n_pad must be a multiple of 128");
   TcJob jb{};
   jb.pb = pb;
   jb.rp = rp;
-  jb.bn = tc_pick_bn(rp.replicas, pb.n_pad);
+  jb.bn = tc_pick_bn_for(pb, rp.replicas);
   TcPlan plan;
   int rc = tc_build_plan(&jb, 1, ws.S16, ws.bytes, ws.status, &plan);
   if (rc) return rc;

@@ -780,22 +780,18 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
       pb.n = p->n;
       pb.n_pad = p->n_pad;
       pb.Jq = p->Jq;
-      pb.fp8 = false;
+      // FP8-stored couplings are read as stored: the kernel's converter warps expand
+      // each staged E4M3 slice to BF16 in shared memory
+      pb.fp8 = p->precision == NMFA_BF16_FP8J;
       pb.inv_d32 = p->inv_d32;
       pb.h32 = p->h32;
       pb.energy_exact = p->energy_exact;
       energy_fused = tc_fuses_energy(pb, rp);
       int64_t bytes = 0;
       if ((rc = tc_workspace_bytes(pb, replicas, &bytes))) return rc;
-      // FP8-stored couplings are expanded to BF16 in front of the kernel's scratch
-      const size_t jexp = p->precision == NMFA_BF16_FP8J ? static_cast<size_t>(p->n_pad) * p->n_pad * 2 : 0;
-      if ((rc = ensure_buf(p->ws, jexp + static_cast<size_t>(bytes), p->done))) return rc;
-      if (jexp) {
-        if ((rc = launch_expand_e4m3_bf16(p->Jq, p->ws.p, static_cast<int64_t>(p->n_pad) * p->n_pad, st))) return rc;
-        pb.Jq = p->ws.p;
-      }
+      if ((rc = ensure_buf(p->ws, static_cast<size_t>(bytes), p->done))) return rc;
       TcWorkspace ws{};
-      ws.S16 = static_cast<char*>(p->ws.p) + jexp;
+      ws.S16 = p->ws.p;
       ws.bytes = bytes;
       ws.status = p->status;
       rc = launch_tc(pb, rp, ws, st);
@@ -950,8 +946,6 @@ struct nmfa_batch {
   std::vector<nmfa_job> jobs;
   std::vector<int> bn;
   std::vector<DevBuf> ws;   // one workspace per plan
-  DevBuf jexp;              // BF16 expansions of FP8-stored couplings
-  std::vector<std::pair<int, size_t>> expand;  // (job, offset into jexp)
   DevBuf signs;             // sign scratch for jobs that did not supply a buffer
   std::vector<int8_t*> signs_ptr;
   std::vector<char> energy_fused;  // per job: energies formed inside the persistent kernel
@@ -972,7 +966,6 @@ static void free_batch(nmfa_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (DevBuf& w : b->ws) pool_free(w.p);
   pool_free(b->signs.p);
-  pool_free(b->jexp.p);
   pool_free(b->status);
   if (b->done) cudaEventDestroy(b->done);
   if (b->own) cudaStreamDestroy(b->own);
@@ -983,12 +976,6 @@ static void free_batch(nmfa_batch* b) {
 // per job) on `st`; the plan was uploaded at creation.
 static int batch_enqueue(nmfa_batch* b, cudaStream_t st) {
   int rc;
-  for (const auto& ex : b->expand) {
-    const nmfa_problem* p = b->problems[ex.first];
-    if ((rc = launch_expand_e4m3_bf16(p->Jq, static_cast<char*>(b->jexp.p) + ex.second,
-                                      static_cast<int64_t>(p->n_pad) * p->n_pad, st)))
-      return rc;
-  }
   for (const TcPlan& plan : b->plans)
     if ((rc = tc_enqueue_plan(plan, false, st))) return rc;
   for (size_t j = 0; j < b->jobs.size(); ++j) {
@@ -1044,13 +1031,6 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
   for (int32_t j = 0; j < count; ++j)
     if (jobs[j].signs_dev == nullptr) sign_bytes += static_cast<size_t>(jobs[j].replicas) * problems[j]->n;
   if (sign_bytes && (rc = ensure_buf(b->signs, sign_bytes))) return fail(rc);
-  size_t jexp_bytes = 0;
-  for (int32_t j = 0; j < count; ++j)
-    if (problems[j]->precision == NMFA_BF16_FP8J) {
-      b->expand.emplace_back(j, jexp_bytes);
-      jexp_bytes += (static_cast<size_t>(problems[j]->n_pad) * problems[j]->n_pad * 2 + 255) / 256 * 256;
-    }
-  if (jexp_bytes && (rc = ensure_buf(b->jexp, jexp_bytes))) return fail(rc);
   std::vector<TcJob> tj(count);
   size_t sp = 0;
   b->signs_ptr.resize(count);
@@ -1067,9 +1047,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.pb.n = p->n;
     t.pb.n_pad = p->n_pad;
     t.pb.Jq = p->Jq;
-    for (const auto& ex : b->expand)
-      if (ex.first == j) t.pb.Jq = static_cast<char*>(b->jexp.p) + ex.second;
-    t.pb.fp8 = false;
+    t.pb.fp8 = p->precision == NMFA_BF16_FP8J;  // read as stored (E4M3), expanded in the kernel
     t.pb.inv_d32 = p->inv_d32;
     t.pb.h32 = p->h32;
     t.pb.energy_exact = p->energy_exact;
@@ -1089,17 +1067,23 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.bn = (options & NMFA_BATCH_BN64) ? 64
            : (options & (NMFA_BATCH_BN128 | NMFA_BATCH_PAIR128)) ? 128
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
-                                             : tc_pick_bn(jb.replicas, p->n_pad);
-    // CTA pairs only on request (where the problem allows them)
-    t.pair = (options & NMFA_BATCH_PAIR128) && tc_use_pair(t.bn, p->n_pad);
+                                             : tc_pick_bn_for(t.pb, jb.replicas);
+    if (t.pb.fp8 && t.bn == 64) t.bn = 128;  // FP8 couplings take 128- or 256-replica tiles
+    // CTA pairs only on request (where the problem allows them; not with FP8 couplings)
+    t.pair = (options & NMFA_BATCH_PAIR128) && !t.pb.fp8 && tc_use_pair(t.bn, p->n_pad);
     b->bn.push_back(t.bn);
   }
   // one persistent launch per tile variant present in the batch
-  const std::pair<int, bool> variants[] = {{256, false}, {128, true}, {128, false}, {64, false}};
-  for (const auto& var : variants) {
+  struct Variant {
+    int bn;
+    bool pair, f8;
+  };
+  const Variant variants[] = {{256, false, false}, {256, false, true}, {128, true, false},
+                              {128, false, false}, {128, false, true}, {64, false, false}};
+  for (const Variant& var : variants) {
     std::vector<TcJob> part;
     for (const TcJob& t : tj)
-      if (t.bn == var.first && t.pair == var.second) part.push_back(t);
+      if (t.bn == var.bn && t.pair == var.pair && t.pb.fp8 == var.f8) part.push_back(t);
     if (part.empty()) continue;
     int64_t bytes = 0;
     if ((rc = tc_plan_bytes(part.data(), static_cast<int32_t>(part.size()), &bytes))) return fail(rc);

@@ -113,14 +113,12 @@ int launch_row_norms_csr(int32_t n, const int32_t* row_ptr, const double* val64,
 int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int64_t rows,
                          int64_t ld, cudaStream_t st);
 int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st);
-// Stored E4M3 couplings -> BF16 copy for the tensor kernel (count a multiple of 16).
-int launch_expand_e4m3_bf16(const void* src, void* dst, int64_t count, cudaStream_t st);
 
 // ---- tcgen05 tensor path ------------------------------------------------------
 struct TcProblem {
   int32_t n;
   int32_t n_pad;          // spins padded to a multiple of 128 (rows and K)
-  const void* Jq;         // BF16 [n_pad][n_pad] or E4M3 [n_pad][n_pad]
+  const void* Jq;         // BF16 [n_pad][n_pad] or (fp8) E4M3 [n_pad][n_pad], read by the kernel as stored
   bool fp8;
   const float* inv_d32;   // n_pad, 0 in padding
   const float* h32;       // h_i in binary32, n_pad (0 in padding)
@@ -154,11 +152,14 @@ struct TcPlan {
   int grid = 0;                      // CTAs launched
   int bn = 128;
   bool pair = false;
+  bool f8 = false;
   int32_t* status = nullptr;
   double makespan = 0.0;             // scheduler's estimate (relative units)
 };
 // Default replicas per tile (64, 128 or 256) of a run of `replicas` replicas of an n_pad problem.
 int tc_pick_bn(int32_t replicas, int32_t n_pad);
+// The same for this problem's storage (FP8-stored couplings take 128 for a pick of 64).
+int tc_pick_bn_for(const TcProblem& pb, int32_t replicas);
 // Whether 128-replica tiles of an n_pad problem run as CTA pairs (results do not change).
 bool tc_use_pair(int bn, int32_t n_pad);
 int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);

@@ -93,8 +93,8 @@ struct nmfa_server {
 
 namespace {
 
-// Device memory a request holds while admitted: its couplings (stored and the BF16
-// expansion a run of FP8-stored J uses), the creation-time FP64 copy, the tensor
+// Device memory a request holds while admitted: its couplings as stored (FP8-stored
+// J is read as stored by the kernel), the creation-time FP64 copy, the tensor
 // kernel's scratch and its inputs/outputs.  The state is counted for the widest tile
 // the library may pick (256 replicas), so admission never under-counts it.
 int64_t request_footprint(const Request* r) {
@@ -103,7 +103,7 @@ int64_t request_footprint(const Request* r) {
   const int64_t r_pad = (r->replicas + bn - 1) / bn * bn;
   const int64_t jq = (r->precision == NMFA_BF16 ? 2 : 1) * n_pad * n_pad;
   const int64_t creation = 8 * n * n;                      // FP64 staging copy held by the problem
-  const int64_t scratch = 2 * n_pad * n_pad + 4 * r_pad * n_pad + (1 << 20);
+  const int64_t scratch = 4 * r_pad * n_pad + (1 << 20);
   const int64_t io = r->replicas * (n + 16) + 8 * r->t_f;
   return jq + n * n + creation + scratch + io;
 }

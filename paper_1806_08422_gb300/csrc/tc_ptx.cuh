@@ -278,6 +278,42 @@ __device__ __forceinline__ void tma_load_2d_pair_warp(uint32_t dst, const void* 
       : "memory");
 }
 
+// ---- FP8 couplings expanded in shared memory ---------------------------------------
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// Makes this thread's generic-proxy shared-memory writes visible to the async proxy
+// (the tensor core reading an operand it did not receive by TMA).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Two E4M3 values (low byte = lower element) -> binary16 x 2, exactly.
+__device__ __forceinline__ uint32_t e4m3x2_to_f16x2(uint32_t two_bytes) {
+  uint32_t r;
+  const uint16_t v = static_cast<uint16_t>(two_bytes);
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"(v));
+  return r;
+}
+// binary16 x 2 holding E4M3 values -> bfloat16 x 2, exactly: (h >> 3) & 0x0FFF is the
+// bfloat16 pattern of |h| 2^-112 (the 5-bit exponent lands in the low bits of the
+// 8-bit one, the 3 significant mantissa bits in the top of the 7), and one bfloat16
+// multiply by +-2^112 (sign taken from h) restores the value.  Every nonzero E4M3
+// value is a normal binary16, so the intermediate is a normal bfloat16 and the
+// product is exact; zero stays zero.
+__device__ __forceinline__ uint32_t f16x2_e4m3_to_bf16x2(uint32_t h) {
+  const uint32_t mag = (h >> 3) & 0x0FFF0FFFu;
+  const uint32_t mul = (h & 0x80008000u) | 0x77807780u;
+  uint32_t r;
+  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(mag), "r"(mul));
+  return r;
+}
+
 // Hardware tanh approximation (MUFU, relative error about 2^-11).
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;

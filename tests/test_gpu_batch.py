@@ -133,6 +133,58 @@ def test_fp8_storage_matches_bf16():
     f.close()
 
 
+def _e4m3_exact_couplings(n, seed):
+    # symmetric couplings drawn from exact E4M3 values: zero, subnormals (k 2^-9),
+    # fractions, integers and the largest finite value
+    vals = np.array([0.0, 2.0 ** -9, 3 * 2.0 ** -9, 7 * 2.0 ** -9, 2.0 ** -6, 0.0625, 0.5, 1.5, 1.0, 3.0, 7.5,
+                     15.0, 26.0, 448.0])
+    rng = np.random.default_rng(seed)
+    U = np.triu(rng.choice(vals, size=(n, n)) * rng.choice([-1.0, 1.0], size=(n, n)), 1)
+    return U + U.T
+
+
+@pytest.mark.parametrize("n,R,tf", [(300, 192, 60), (1000, 64, 40), (2048, 2048, 20)])
+def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
+    # FP8-stored couplings reach the tensor cores through the kernel's converter warps
+    # (E4M3 slice -> BF16 operand in shared memory); the run equals the same couplings
+    # stored in BF16 bit for bit, for every exact E4M3 value, whatever tile width each
+    # storage takes (FP8 takes 128 where BF16 takes 64, and 256-wide tiles for
+    # n = 2048 with 2048 replicas).
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = _e4m3_exact_couplings(n, 40 + n)
+    T = torch.as_tensor(inst.schedule(tf), device=dev)
+    a = nmfa.Problem(J, precision="bf16")
+    f = nmfa.Problem(J, precision="bf16_fp8j")
+    assert f.info()["device_bytes"] < a.info()["device_bytes"]
+    res = {}
+    for name, p in (("bf16", a), ("fp8", f)):
+        sb = torch.empty((R, n), dtype=torch.int8, device=dev)
+        eb = torch.empty(R, dtype=torch.float64, device=dev)  # real-valued couplings: FP64 energies
+        b = nmfa.nmfa_batch_create([p.handle], [nmfa.make_job(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=sb,
+                                                              energy=eb)], 0)
+        res[name + "_plan"] = nmfa.nmfa_batch_plan(b)
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        nmfa.nmfa_batch_destroy(b)
+        res[name + "_batch"] = (sb.cpu().numpy(), eb.cpu().numpy())
+        s = torch.empty((R, n), dtype=torch.int8, device=dev)
+        e = torch.empty(R, dtype=torch.float64, device=dev)
+        p.run_device(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=s, energy=e)
+        p.sync()
+        res[name] = (s.cpu().numpy(), e.cpu().numpy())
+    assert res["fp8_plan"][0][0] in (128, 256), res["fp8_plan"]
+    if n == 2048:
+        assert res["fp8_plan"] == [(256, 1, 1)] == res["bf16_plan"]
+    np.testing.assert_array_equal(res["fp8"][0], res["bf16"][0])
+    np.testing.assert_array_equal(res["fp8"][1], res["bf16"][1])
+    np.testing.assert_array_equal(res["fp8_batch"][0], res["fp8"][0])  # batched = alone
+    for r in (0, R - 1):
+        assert abs(res["fp8"][1][r] - oracle.energy(J, res["fp8"][0][r])) <= 1e-12 * np.abs(np.triu(J, 1)).sum()
+    a.close()
+    f.close()
+
+
 def test_mixed_precision_and_width_batch():
     torch, dev = _dev()
     from paper_1806_08422_gb300 import nmfa
