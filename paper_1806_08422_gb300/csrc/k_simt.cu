@@ -846,7 +846,10 @@ __global__ void convert_dense_kernel(int n, const double* __restrict__ J64, void
   const int64_t total = rows * ld;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = idx / ld, j = idx % ld;
+    const int64_t i = idx / ld, j0 = idx % ld;
+    // E4M3 (kind 2) rows keep each group of four values in the order (k0, k2, k1, k3),
+    // the order the tensor kernel's converter reads (ld is a multiple of 4)
+    const int64_t j = kind == 2 ? ((j0 & ~int64_t(3)) | ((j0 & 1) << 1) | ((j0 >> 1) & 1)) : j0;
     const double v = (i < n && j < n) ? J64[i * n + j] : 0.0;
     store_kind(dst, idx, v, kind);
   }

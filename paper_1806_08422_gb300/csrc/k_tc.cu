@@ -94,11 +94,13 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   lands 48 KB of operands per 128-deep K slice instead of 64 KB, and the tensor
 //   core reads 96 instead of 128 bytes per clock from each SM's shared memory (at
 //   the full MMA rate).  Ring of 4 slots of 48 KB; the even CTA issues the MMAs.
-//   FP8 (F8 = true, 128 or 256 replicas, one CTA per tile): J is stored in E4M3; its
-//   slices go by TMA into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes)
-//   and two converter warps write them as BF16 into the slot's A operand (the MMA
-//   stays kind::f16 with both operands BF16); the slot's full barrier then also
-//   waits for both converter warps.
+//   FP8 (F8 = true, 128 or 256 replicas, one CTA per tile): J is stored in E4M3 (in
+//   the byte order (k0, k2, k1, k3) within each 4-value group); its slices go by TMA
+//   into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes) and are written as
+//   BF16 into the slot's A operand (the MMA stays kind::f16 with both operands BF16)
+//   by two converter warps, half of each slice each (a third would put six warps on
+//   one scheduler, whose register file then allows 80 registers a thread instead of
+//   96); the slot's full barrier then also waits for both converter warps.
 template <int BN, bool PAIR = false, bool F8 = false>
 struct TcShape {
   static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
@@ -182,7 +184,7 @@ struct SharedCtl {
   // epilogue warps arrive from the other CTA), so each CTA copies the pair's other
   // row block without a round trip through that block's epoch counter.
   uint64_t pair_pub;
-  // FP8: staged E4M3 slice landed (TMA) / consumed by both converter warps
+  // FP8: staged E4M3 slice landed (TMA) / converted by all of its tasks
   uint64_t stg_full[2];
   uint64_t stg_empty[2];
   uint64_t drain;
@@ -259,6 +261,75 @@ __device__ __forceinline__ bool wait_block(const uint32_t* f0, int nb, int k, ui
 
 // The tensor maps live in global memory (written by an earlier kernel); make the
 // tensormap proxy see those writes before the first copy that uses them.
+// ---------------------------------------------------------------- FP8 conversion
+// A staged E4M3 slice of fill f (128 rows x 128 K values, 128-byte swizzle) becomes
+// the BF16 A operand of ring slot f % kStages (two 128-byte-swizzle atoms of 64 K
+// values).  Each converter warp takes every fill in order and converts its share of
+// the slice's kConvParts parts of 16 rows, so it waits on the staging barriers and
+// on the slots' empty barriers in fill order and never one phase ahead.  The
+// producer stages fill f's slice before it waits for the ring slot (the copy
+// overlaps the MMAs still reading the slot); the converter waits for the slot to be
+// released before it writes, then arrives on the staging buffer's empty barrier and
+// on the slot's full barrier (one arrival per converter warp each).
+constexpr uint32_t kConvParts = 8;
+
+// Rows 16 part .. 16 part + 15 of a staged slice -> BF16 atoms; lane l converts the
+// 16-byte chunks l, l + 32, l + 64, l + 96 of the part (row 16 part + l / 8 + 4 u,
+// K values 16 (l % 8) .. + 15), ILP chunks at a time.
+template <int ILP>
+__device__ __forceinline__ void convert_part(uint32_t src, uint32_t dst, uint32_t part, int lane) {
+  const uint32_t c = static_cast<uint32_t>(lane & 7);
+  const uint32_t r0 = part * 16u + static_cast<uint32_t>(lane >> 3);
+  // atom c / 4 holds K 64 (c / 4) .. + 63; the chunk's 16 values fill chunks
+  // 2 (c % 4) and 2 (c % 4) + 1 of the row there
+  const uint32_t atom = dst + (c >> 2) * kABytes;
+  const uint32_t c0 = 2u * (c & 3u);
+#pragma unroll
+  for (int u0 = 0; u0 < 4; u0 += ILP) {
+    uint4 v[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const uint32_t r = r0 + 4u * static_cast<uint32_t>(u0 + u);
+      v[u] = ptx::ld_shared_v4(src + r * 128u + ((c ^ (r & 7u)) << 4));
+    }
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const uint32_t r = r0 + 4u * static_cast<uint32_t>(u0 + u);
+      const uint32_t sw = r & 7u;
+      uint4 lo, hi;  // BF16 values 16c .. 16c + 7 and 16c + 8 .. 16c + 15
+      ptx::e4m3x4p_to_bf16x2x2(v[u].x, lo.x, lo.y);
+      ptx::e4m3x4p_to_bf16x2x2(v[u].y, lo.z, lo.w);
+      ptx::e4m3x4p_to_bf16x2x2(v[u].z, hi.x, hi.y);
+      ptx::e4m3x4p_to_bf16x2x2(v[u].w, hi.z, hi.w);
+      const uint32_t row = atom + r * 128u;
+      ptx::st_shared_v4(row + ((c0 ^ sw) << 4), lo);
+      ptx::st_shared_v4(row + (((c0 + 1u) ^ sw) << 4), hi);
+    }
+  }
+}
+
+// Converter warp cw's share of fill f: parts cw, cw + kConvWarps, ...
+template <int BN>
+__device__ __forceinline__ bool conv_fill(SharedCtl* ctl, int32_t* status, uint32_t ring, uint32_t stg, uint32_t f,
+                                          int cw, int lane) {
+  using Shape = TcShape<BN, false, true>;
+  constexpr uint32_t kStages = static_cast<uint32_t>(Shape::kStages);
+  const uint32_t jb = f & 1u, st = f % kStages;
+  if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->stg_full[jb]), (f >> 1) & 1u, ctl, status))) return false;
+  if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->empty[st]), ((f / kStages) & 1u) ^ 1u, ctl, status)))
+    return false;
+#pragma unroll 1
+  for (uint32_t part = static_cast<uint32_t>(cw); part < kConvParts; part += Shape::kConvWarps)
+    convert_part<4>(stg + jb * Shape::kStgBytes, ring + st * Shape::kStageBytes, part, lane);
+  ptx::fence_proxy_async_shared();
+  __syncwarp();
+  if (lane == 0) {
+    ptx::mbar_arrive(ptx::smem_u32(&ctl->stg_empty[jb]));
+    ptx::mbar_arrive(ptx::smem_u32(&ctl->full[st]));
+  }
+  return true;
+}
+
 __device__ __forceinline__ void acquire_tensormap(const void* m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
                : "memory");
@@ -616,6 +687,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     const bool lead = crank == 0u;
     uint32_t stage = 0, phase = 0;  // next ring slot to fill
     uint32_t filled = 0;            // ring slots whose copies were issued (for the drain)
+    uint32_t staged = 0;            // FP8: staging copies issued (for the drain)
     uint32_t own_pubs = 0;          // own_pub (and pair_pub) phases completed by earlier items
     bool ok = true;
     auto load = [&](uint32_t dst, const void* tm, int x, int y, uint32_t st) {
@@ -646,6 +718,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
             return false;
           ptx::mbar_arrive_expect_tx_warp(stg_full0 + 8u * jb, Shape::kStgBytes);
           ptx::tma_load_2d_warp(stg_base + jb * Shape::kStgBytes, tmJ, ks * kKSlot, b * kBM, stg_full0 + 8u * jb);
+          ++staged;
         } else {
 #pragma unroll
           for (int a = 0; a < kAtoms; ++a) load(ring + st * kStageBytes + a * kABytes, tmJ, ks * kKSlot + a * kBK, b * kBM, st);
@@ -669,11 +742,16 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
         int claimed = 0;
         int ks = kslice_base;  // K slice of loop index kb
         for (int kb = 0; kb < pre; ++kb) {
+          // FP8: the E4M3 slice is staged before the slot is free (the conversion
+          // tasks wait for the slot)
+          if constexpr (F8) {
+            ok = load_j(ks, stage, filled);
+            if (!ok) break;
+          }
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
           if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-          ok = load_j(ks, stage, filled);
-          if (!ok) break;
+          if constexpr (!F8) load_j(ks, stage, filled);
           ++claimed;
           ++filled;
           if (++stage == kStages) {
@@ -715,12 +793,16 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
         }
         if (!ok) break;
         for (int kb = pre; kb < KB; ++kb) {
+          if constexpr (F8) {
+            ok = load_j(ks, stage, filled);
+            if (!ok) break;
+          }
           ok = __all_sync(0xffffffffu, wait_bar(empty0 + 8u * stage, phase ^ 1u, &ctl, status));
           if (!ok) break;
           const uint32_t sA = ring + stage * kStageBytes;
           if (lead) ptx::mbar_arrive_expect_tx_warp(full0 + 8u * stage, stage_tx);
-          ok = load_j(ks, stage, filled);
-          if (ok) ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
+          if constexpr (!F8) load_j(ks, stage, filled);
+          ok = wait_block(gflags, nb, ks, need, lane, seen, &ctl, status, t == 0);
 #pragma unroll
           for (int a = 0; a < kAtoms; ++a)
             load(sA + kAtoms * kABytes + a * kBAtomBytes, tmS, ks * kKSlot + a * kBK, sy, stage);
@@ -742,7 +824,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       const uint32_t last = filled;
       if constexpr (F8) {
         // the staged E4M3 copies of the last fills (their barriers complete on landing)
-        for (uint32_t k = (last > 2u ? last - 2u : 0u); k < last; ++k) {
+        for (uint32_t k = (staged > 2u ? staged - 2u : 0u); k < staged; ++k) {
           const uint64_t t0 = ptx::globaltimer_ns();
           while (!ptx::mbar_try_wait(stg_full0 + 8u * (k & 1u), (k >> 1) & 1u) && ptx::globaltimer_ns() - t0 < kDrainNs) {
           }
@@ -838,68 +920,14 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
     }
   } else if (F8 && lw >= 2 + kEpiWarps) {
     // ------------------------------------------------------------ FP8 converters
-    // Both warps walk the producer's fill sequence.  Fill f's E4M3 slice (128 rows of
-    // 128 bytes, 128-byte swizzle) becomes the BF16 A operand of ring slot f % kStages
-    // (two 128-byte-swizzle atoms of 64 K values): each thread takes 16-byte chunks,
-    // converts its 16 values and writes two 16-byte BF16 chunks.  The slot is free: the
-    // producer issued this fill's staging copy only after the slot's empty barrier.
-    const int ct = (lw - 2 - kEpiWarps) * 32 + lane;  // 0 .. 63
-    const uint32_t full0 = ptx::smem_u32(&ctl.full[0]);
-    const uint32_t stg_full0 = ptx::smem_u32(&ctl.stg_full[0]), stg_empty0 = ptx::smem_u32(&ctl.stg_empty[0]);
-    uint32_t fill = 0;
-    bool ok = true;
-    for (int w = w_begin; w < w_end && ok; ++w) {
-      const TcGroup* g = groups + items[w].group;
-      const int KB = g->n_pad / kKSlot, steps = g->t_f + g->energy_pass;
-      for (int t = 0; t < steps && ok; ++t) {
-        for (int kb = 0; kb < KB; ++kb, ++fill) {
-          const uint32_t jb = fill & 1u, st = fill % kStages;
-          ok = __all_sync(0xffffffffu, wait_bar(stg_full0 + 8u * jb, (fill >> 1) & 1u, &ctl, status));
-          if (!ok) break;
-          const uint32_t src = stg_base + jb * Shape::kStgBytes;
-          const uint32_t dst = ring + st * kStageBytes;
-          // four chunks per round: their loads, then their conversions, then their
-          // stores, so that each thread has independent work in flight
-          constexpr int kChunks = (kBM * kKSlot / 16) / 64;  // 16 per thread
-#pragma unroll 1
-          for (int it0 = 0; it0 < kChunks; it0 += 4) {
-            uint4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = ct + 64 * (it0 + u);  // 16-byte chunk of the slice
-              const int r = q >> 3, c = q & 7;     // row, K values 16c .. 16c + 15
-              v[u] = ptx::ld_shared_v4(src + static_cast<uint32_t>(r) * 128u +
-                                       ((static_cast<uint32_t>(c) ^ static_cast<uint32_t>(r & 7)) << 4));
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = ct + 64 * (it0 + u);
-              const int r = q >> 3, c = q & 7;
-              const uint32_t sw = static_cast<uint32_t>(r & 7);
-              uint4 lo, hi;  // BF16 values 16c .. 16c+7 and 16c+8 .. 16c+15
-              lo.x = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].x));
-              lo.y = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].x >> 16));
-              lo.z = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].y));
-              lo.w = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].y >> 16));
-              hi.x = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].z));
-              hi.y = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].z >> 16));
-              hi.z = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].w));
-              hi.w = ptx::f16x2_e4m3_to_bf16x2(ptx::e4m3x2_to_f16x2(v[u].w >> 16));
-              // atom c / 4 holds K 64 (c / 4) .. +63; chunks 2 (c % 4) and the next of row r
-              const uint32_t atom = dst + static_cast<uint32_t>(c >> 2) * kABytes + static_cast<uint32_t>(r) * 128u;
-              const uint32_t c0 = static_cast<uint32_t>(2 * (c & 3));
-              ptx::st_shared_v4(atom + ((c0 ^ sw) << 4), lo);
-              ptx::st_shared_v4(atom + (((c0 + 1u) ^ sw) << 4), hi);
-            }
-          }
-          ptx::fence_proxy_async_shared();
-          __syncwarp();
-          if (lane == 0) {
-            ptx::mbar_arrive(stg_empty0 + 8u * jb);
-            ptx::mbar_arrive(full0 + 8u * st);
-          }
-        }
+    if constexpr (F8) {
+      uint32_t total = 0;  // ring fills of this pipeline
+      for (int w = w_begin; w < w_end; ++w) {
+        const TcGroup* g = groups + items[w].group;
+        total += static_cast<uint32_t>((g->t_f + g->energy_pass) * (g->n_pad / kKSlot));
       }
+      for (uint32_t f = 0; f < total; ++f)
+        if (!conv_fill<BN>(&ctl, status, ring, stg_base, f, lw - 2 - kEpiWarps, lane)) break;
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -943,7 +971,7 @@ nmfa_tc_kernel(const TcGroup* __restrict__ groups, const TcItem* __restrict__ it
       }
       for (int j = 0; j < 2; ++j) {
         ptx::mbar_init(ptx::smem_u32(&c.stg_full[j]), 1);
-        ptx::mbar_init(ptx::smem_u32(&c.stg_empty[j]), Shape::kConvWarps > 0 ? Shape::kConvWarps : 1);
+        ptx::mbar_init(ptx::smem_u32(&c.stg_empty[j]), F8 ? Shape::kConvWarps : 1);
       }
       ptx::mbar_init(ptx::smem_u32(&c.acc_full), 1);
       // a pair's MMA issuer waits for the bias of both CTAs' epilogue warps

@@ -130,7 +130,7 @@ struct nmfa_problem {
   float* inv_d32 = nullptr;
   float* h32 = nullptr;
   float* J32 = nullptr;
-  void* Jq = nullptr;      // bf16 / e4m3 padded
+  void* Jq = nullptr;      // bf16 / e4m3 padded (e4m3: groups of four as k0, k2, k1, k3)
   int8_t* J8 = nullptr;    // energy copy, rows padded to 16 bytes
   int32_t* row_ptr = nullptr;
   int32_t* col = nullptr;
@@ -347,7 +347,8 @@ void compact_rows(int32_t n, int32_t n_pad, const double* h, const double* J, bo
         sq += v * v;
         hc->J8[i * hc->ld8 + j] = static_cast<int8_t>(v);
         if (fp8) {
-          hc->Jq[i * lp + j] = e4m3_bits(v);
+          // groups of four in the order (k0, k2, k1, k3), as the tensor kernel reads them
+          hc->Jq[i * lp + ((j & ~3) | ((j & 1) << 1) | ((j >> 1) & 1))] = e4m3_bits(v);
         } else {
           const uint16_t b = bf16_bits(v);
           std::memcpy(&hc->Jq[2 * (i * lp + j)], &b, 2);

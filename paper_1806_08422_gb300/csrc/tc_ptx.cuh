@@ -43,6 +43,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Non-blocking test of a phase (no suspension while the phase is pending).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 
 // ---- TMA ----------------------------------------------------------------------
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
@@ -312,6 +322,29 @@ __device__ __forceinline__ uint32_t f16x2_e4m3_to_bf16x2(uint32_t h) {
   uint32_t r;
   asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(mag), "r"(mul));
   return r;
+}
+// Four E4M3 values stored in the byte order (k0, k2, k1, k3) -> bfloat16 pairs
+// lo = (k0, k1) and hi = (k2, k3), exactly, without a conversion instruction.  For a
+// value b = s eeee mmm, the bfloat16 pattern (eeee mmm) << 4 (exponent field
+// 0000eeee, mantissa mmm0000) is |b| 2^-120 (subnormal when eeee = 0, exactly
+// mmm 2^-129), and one bfloat16 multiply by +-2^120 (0x7B80, sign of b) restores the
+// value; the products are normal or zero and exact.  The storage order puts k0, k1
+// in bytes 0 and 2 (signs at bits 7 and 23: shifted by 8 to the halves' sign bits)
+// and k2, k3 in bytes 1 and 3 (signs already at bits 15 and 31).
+__device__ __forceinline__ void e4m3x4p_to_bf16x2x2(uint32_t v, uint32_t& lo, uint32_t& hi) {
+  const uint32_t mag_lo = (v << 4) & 0x07F007F0u, mul_lo = ((v << 8) & 0x80008000u) | 0x7B807B80u;
+  const uint32_t mag_hi = (v >> 4) & 0x07F007F0u, mul_hi = (v & 0x80008000u) | 0x7B807B80u;
+  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(lo) : "r"(mag_lo), "r"(mul_lo));
+  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hi) : "r"(mag_hi), "r"(mul_hi));
+}
+// Shared-memory word with CTA-scope acquire / release ordering.
+__device__ __forceinline__ uint32_t ld_acquire_shared(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_shared(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 
 // Hardware tanh approximation (MUFU, relative error about 2^-11).
