@@ -212,6 +212,7 @@ typedef struct nmfa_batch nmfa_batch;
 #define NMFA_BATCH_AUTOTUNE 2 /* pick replicas per tile (64/128/256) per job by timing */
 #define NMFA_BATCH_BN64 4     /* force 64 replicas per tile (results do not change) */
 #define NMFA_BATCH_BN128 16   /* force 128 replicas per tile, one CTA per tile (results do not change) */
+#define NMFA_BATCH_BN256 64   /* force 256 replicas per tile (results do not change) */
 /* Run 128 replicas per tile as CTA pairs (two CTAs sharing one cta_group::2 MMA of
  * M = 256, each loading half of every state slice) wherever the problem allows it
  * (n rounded to 128 is a multiple of 256 and the pairs fit on the grid).  Not the

@@ -259,8 +259,6 @@ __device__ __forceinline__ bool wait_block(const uint32_t* f0, int nb, int k, ui
   }
 }
 
-// The tensor maps live in global memory (written by an earlier kernel); make the
-// tensormap proxy see those writes before the first copy that uses them.
 // ---------------------------------------------------------------- FP8 conversion
 // A staged E4M3 slice of fill f (128 rows x 128 K values, 128-byte swizzle) becomes
 // the BF16 A operand of ring slot f % kStages (two 128-byte-swizzle atoms of 64 K
@@ -330,6 +328,8 @@ __device__ __forceinline__ bool conv_fill(SharedCtl* ctl, int32_t* status, uint3
   return true;
 }
 
+// The tensor maps live in global memory (written by an earlier kernel); make the
+// tensormap proxy see those writes before the first copy that uses them.
 __device__ __forceinline__ void acquire_tensormap(const void* m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
                : "memory");
@@ -1434,6 +1434,11 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
 // FP8-stored couplings take one-CTA 128- or 256-replica tiles (two converter warps
 // beside a pipeline's 18; the 64-replica CTA's two pipelines leave no room).  Results
 // do not depend on the width.
+// FP8-stored couplings take the same widths, except 128 where BF16 would take 64
+// (the FP8 kernel has no 64-replica form).  256-replica tiles convert each J slice
+// once for twice the replicas, but on half the SMs: SK runs of 200 steps, us per step
+// with 256- against 128-replica tiles: n = 4096, R = 512: 38.5 / 34.2; n = 2000,
+// R = 1024: 23.2 / 18.7; n = 512, R = 1024: 12.1 / 7.0.
 int tc_pick_bn_for(const TcProblem& pb, int32_t replicas) {
   const int bn = tc_pick_bn(replicas, pb.n_pad);
   return (pb.fp8 && bn == 64) ? 128 : bn;

@@ -1067,6 +1067,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     b->energy_fused.push_back(tc_fuses_energy(t.pb, t.rp) ? 1 : 0);
     t.bn = (options & NMFA_BATCH_BN64) ? 64
            : (options & (NMFA_BATCH_BN128 | NMFA_BATCH_PAIR128)) ? 128
+           : (options & NMFA_BATCH_BN256) ? 256
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
                                              : tc_pick_bn_for(t.pb, jb.replicas);
     if (t.pb.fp8 && t.bn == 64) t.bn = 128;  // FP8 couplings take 128- or 256-replica tiles

@@ -227,6 +227,7 @@ NMFA_BATCH_AUTOTUNE = 2
 NMFA_BATCH_BN64 = 4
 NMFA_BATCH_BN128 = 16
 NMFA_BATCH_PAIR128 = 32
+NMFA_BATCH_BN256 = 64
 NMFA_BATCH_DEBUG_WITHHOLD_TILE = 8
 
 

@@ -8,7 +8,7 @@ the burst BF16 peak of MEASURED_PEAKS.json, and the best energy.  Both storages 
 same instance give bit-identical runs, so their energies must agree.
 
     python -m paper_1806_08422_gb300.sizes [--sizes 8192:512,2000:1024] [--t-f 200]
-                                           [--storage bf16,bf16_fp8j] [--reps 3]
+                                           [--storage bf16,bf16_fp8j] [--reps 3] [--options 0]
 
 Prints one JSON line.  This module only drives the C ABI.
 """
@@ -33,7 +33,7 @@ def burst_peak():
         return 1900.0
 
 
-def time_one(J, R, t_f, storage, reps):
+def time_one(J, R, t_f, storage, reps, options=0):
     import torch
     dev = torch.device("cuda", 0)
     n = J.shape[0]
@@ -42,7 +42,7 @@ def time_one(J, R, t_f, storage, reps):
     s = torch.empty((R, n), dtype=torch.int8, device=dev)
     e = torch.empty(R, dtype=torch.int64, device=dev)
     st = torch.cuda.Stream()
-    b = nmfa.nmfa_batch_create([p.handle], [nmfa.make_job(T, 0.15, 0.15, R, signs=s, energy_i64=e)], 0)
+    b = nmfa.nmfa_batch_create([p.handle], [nmfa.make_job(T, 0.15, 0.15, R, signs=s, energy_i64=e)], options)
     try:
         nmfa.nmfa_batch_launch(b, st)  # warm-up
         nmfa.nmfa_batch_sync(b)
@@ -73,6 +73,8 @@ def main():
     ap.add_argument("--storage", default="bf16,bf16_fp8j")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--options", type=int, default=0,
+                    help="nmfa_batch_create options, e.g. 16 / 64 to force 128 / 256 replicas per tile")
     args = ap.parse_args()
     peak = burst_peak()
     out = []
@@ -81,11 +83,11 @@ def main():
         J = inst.sk(n, args.seed)
         row = {"n": n, "replicas": R}
         for storage in args.storage.split(","):
-            r = time_one(J, R, args.t_f, storage, args.reps)
+            r = time_one(J, R, args.t_f, storage, args.reps, args.options)
             r["frac_of_burst_bf16"] = r["tflops"] / peak
             row[storage] = r
         out.append(row)
-    print(json.dumps({"t_f": args.t_f, "burst_bf16_tflops": peak, "runs": out}))
+    print(json.dumps({"t_f": args.t_f, "options": args.options, "burst_bf16_tflops": peak, "runs": out}))
 
 
 if __name__ == "__main__":

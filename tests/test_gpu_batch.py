@@ -173,7 +173,7 @@ def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
         p.run_device(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=s, energy=e)
         p.sync()
         res[name] = (s.cpu().numpy(), e.cpu().numpy())
-    assert res["fp8_plan"][0][0] in (128, 256), res["fp8_plan"]
+    assert res["fp8_plan"] == [(256 if n == 2048 else 128, 1, 1)], res["fp8_plan"]
     if n == 2048:
         assert res["fp8_plan"] == [(256, 1, 1)] == res["bf16_plan"]
     np.testing.assert_array_equal(res["fp8"][0], res["bf16"][0])
@@ -260,6 +260,32 @@ def test_256_replica_tiles_match_64_replica_tiles():
     np.testing.assert_array_equal(s, s256)
     for r in (0, 777, R - 1):
         assert e256[r] == oracle.energy_i64(J, s256[r])
+    p.close()
+
+
+@pytest.mark.parametrize("n,R,storage", [(300, 200, "bf16"), (1000, 300, "bf16_fp8j"), (129, 64, "bf16")])
+def test_forced_256_replica_tiles_match_128_replica_tiles(n, R, storage):
+    # NMFA_BATCH_BN256 forces 256-replica tiles (one accumulator; short K sweeps of
+    # one to eight slices; a replica block that is partly padding): signs and Eq. (1)
+    # energies equal those of 128-replica tiles bit for bit, and the energies are
+    # exact against the oracle.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    J = inst.sk(n, 90 + n)
+    p = nmfa.Problem(J, precision=storage)
+    T = torch.as_tensor(inst.schedule(40), device=dev)
+    res = {}
+    for name, options, bn in (("bn256", nmfa.NMFA_BATCH_BN256, 256), ("bn128", nmfa.NMFA_BATCH_BN128, 128)):
+        b, outs = _batch([p], [(T, R, 5, 2)], options)
+        assert nmfa.nmfa_batch_plan(b) == [(bn, 1, 1)], (name, nmfa.nmfa_batch_plan(b))
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        res[name] = (outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy())
+        nmfa.nmfa_batch_destroy(b)
+    np.testing.assert_array_equal(res["bn256"][0], res["bn128"][0])
+    np.testing.assert_array_equal(res["bn256"][1], res["bn128"][1])
+    for r in (0, R - 1):
+        assert res["bn256"][1][r] == oracle.energy_i64(J, res["bn256"][0][r])
     p.close()
 
 
