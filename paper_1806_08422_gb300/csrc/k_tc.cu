@@ -1432,10 +1432,9 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
 }
 
 // FP8-stored couplings take one-CTA 128- or 256-replica tiles (two converter warps
-// beside a pipeline's 18; the 64-replica CTA's two pipelines leave no room).  Results
-// do not depend on the width.
-// FP8-stored couplings take the same widths, except 128 where BF16 would take 64
-// (the FP8 kernel has no 64-replica form).  256-replica tiles convert each J slice
+// beside a pipeline's 18; the 64-replica CTA's two pipelines leave no room), the
+// BF16 widths except 128 where BF16 would take 64.  Results do not depend on the
+// width.  256-replica tiles convert each J slice
 // once for twice the replicas, but on half the SMs: SK runs of 200 steps, us per step
 // with 256- against 128-replica tiles: n = 4096, R = 512: 38.5 / 34.2; n = 2000,
 // R = 1024: 23.2 / 18.7; n = 512, R = 1024: 12.1 / 7.0.

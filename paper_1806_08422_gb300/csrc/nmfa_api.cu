@@ -1048,7 +1048,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.pb.n = p->n;
     t.pb.n_pad = p->n_pad;
     t.pb.Jq = p->Jq;
-    t.pb.fp8 = p->precision == NMFA_BF16_FP8J;  // read as stored (E4M3), expanded in the kernel
+    t.pb.fp8 = p->precision == NMFA_BF16_FP8J;  // read as stored (E4M3), widened to BF16 in the kernel
     t.pb.inv_d32 = p->inv_d32;
     t.pb.h32 = p->h32;
     t.pb.energy_exact = p->energy_exact;
