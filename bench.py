@@ -353,6 +353,7 @@ def leg_served(rate=200.0, duration=0.5, n_lo=64, n_hi=2048, fp32_cap=30.0):
                         "(G(N,0.5)); up to 4 attempts (attempt k on noise stream k)"
                         % (rate, duration, len(reqs), n_lo, n_hi),
             "tensor_server": dict(summary(srv, srv["requests"]), launches=srv["launches"],
+                                  batches_reused=srv["batches_reused"],
                                   mean_attempts=srv["mean_attempts"], precision="BF16 J and S"),
             "fp32_per_instance": dict(summary(f32, f32["served"]), time_cap_s=fp32_cap,
                                       note="served one request at a time in arrival order; requests not started "

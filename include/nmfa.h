@@ -244,6 +244,13 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
 int nmfa_batch_launch(nmfa_batch* b, void* cuda_stream);
 /* Waits for the last execution; NMFA_ETIMEOUT if a device-side wait gave up. */
 int nmfa_batch_sync(nmfa_batch* b);
+/* Re-targets the batch at other noise streams (Algorithm 1's Gaussian draws of job j
+ * come from stream stream_ids[j] from the next execution on), keeping its plan and
+ * workspace: a rerun of the same jobs with fresh noise needs no new batch.  Host array
+ * of `count` = the batch's job count; ordered after the previous execution (the new
+ * descriptors are uploaded on the batch's own stream).  NMFA_EINVAL on a count
+ * mismatch; the batch is unchanged then. */
+int nmfa_batch_set_stream_ids(nmfa_batch* b, const uint32_t* stream_ids, int32_t count);
 /* Persistent grid size, number of replica-block groups, workspace bytes. */
 int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t* workspace_bytes);
 void nmfa_batch_destroy(nmfa_batch* b);
@@ -312,9 +319,11 @@ int nmfa_server_poll(nmfa_server* s, uint64_t ticket, nmfa_result* out, int8_t* 
 /* Waits until every submitted request is done (NMFA_ETIMEOUT after timeout_s). */
 int nmfa_server_drain(nmfa_server* s, double timeout_s);
 /* Persistent launches so far, device memory held by admitted requests, requests not
- * finished, and the most requests one launch has carried (any pointer may be NULL). */
+ * finished, the most requests one launch has carried, and the launches that reused
+ * the batch (plan and workspace) of their requests' previous attempt (any pointer
+ * may be NULL). */
 int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding,
-                      int32_t* max_requests_per_launch);
+                      int32_t* max_requests_per_launch, int64_t* batches_reused);
 /* Stops the loop (waits for launches on the GPU) and frees everything. */
 void nmfa_server_destroy(nmfa_server* s);
 

@@ -1276,11 +1276,13 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   const size_t off_state = off_e2h + align_up(gl.size() * static_cast<size_t>(jobs[0].bn) * 8, 256);
   // group descriptors
   plan->host.assign(off_flags, 0);
+  plan->group_job.resize(gl.size());
   TcGroup* hg = reinterpret_cast<TcGroup*>(plan->host.data());
   size_t flag_pos = 0, state_pos = off_state;
   std::vector<uint32_t*> gflags(gl.size());
   for (size_t k = 0; k < gl.size(); ++k) {
     const TcJob& jb = jobs[gl[k].job];
+    plan->group_job[k] = gl[k].job;
     TcGroup& g = hg[k];
     const int bn = jb.bn;
     g.n = jb.pb.n;
@@ -1360,6 +1362,11 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   plan->status = status;
   plan->makespan = *std::max_element(free_at.begin(), free_at.end());
   return NMFA_OK;
+}
+
+void tc_plan_set_streams(TcPlan* plan, const uint32_t* stream_ids) {
+  TcGroup* hg = reinterpret_cast<TcGroup*>(plan->host.data() + plan->groups_off);
+  for (size_t k = 0; k < plan->group_job.size(); ++k) hg[k].stream = stream_ids[plan->group_job[k]];
 }
 
 // Upload the plan (group descriptors, items, per-pipeline offsets) from kernel

@@ -952,6 +952,7 @@ struct nmfa_batch {
   std::vector<char> energy_fused;  // per job: energies formed inside the persistent kernel
   int32_t* status = nullptr;
   std::vector<TcPlan> plans;  // one persistent launch per tile width in the batch
+  std::vector<std::vector<int32_t>> plan_jobs;  // per plan: the batch index of each of its jobs
   cudaStream_t own = nullptr;
   cudaEvent_t done = nullptr;
   cudaGraph_t graph = nullptr;
@@ -1084,14 +1085,21 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
                               {128, false, false}, {128, false, true}, {64, false, false}};
   for (const Variant& var : variants) {
     std::vector<TcJob> part;
-    for (const TcJob& t : tj)
-      if (t.bn == var.bn && t.pair == var.pair && t.pb.fp8 == var.f8) part.push_back(t);
+    std::vector<int32_t> part_jobs;
+    for (size_t j = 0; j < tj.size(); ++j) {
+      const TcJob& t = tj[j];
+      if (t.bn == var.bn && t.pair == var.pair && t.pb.fp8 == var.f8) {
+        part.push_back(t);
+        part_jobs.push_back(static_cast<int32_t>(j));
+      }
+    }
     if (part.empty()) continue;
     int64_t bytes = 0;
     if ((rc = tc_plan_bytes(part.data(), static_cast<int32_t>(part.size()), &bytes))) return fail(rc);
     b->ws.emplace_back();
     if ((rc = ensure_buf(b->ws.back(), static_cast<size_t>(bytes)))) return fail(rc);
     b->plans.emplace_back();
+    b->plan_jobs.push_back(part_jobs);
     const bool withhold = (options & NMFA_BATCH_DEBUG_WITHHOLD_TILE) && b->plans.size() == 1;  // the first plan
     if (withhold && part[0].pb.n_pad <= 128) return fail(set_error(NMFA_EINVAL, "withheld tile needs n > 128"));
     if ((rc = tc_build_plan(part.data(), static_cast<int32_t>(part.size()), b->ws.back().p, bytes, b->status,
@@ -1132,6 +1140,24 @@ int nmfa_batch_launch(nmfa_batch* b, void* cuda_stream) {
     return rc;
   }
   return cuda_error(cudaEventRecord(b->done, st), "event record");
+}
+
+int nmfa_batch_set_stream_ids(nmfa_batch* b, const uint32_t* stream_ids, int32_t count) {
+  if (b == nullptr || stream_ids == nullptr) return set_error(NMFA_EINVAL, "NULL argument");
+  if (count != static_cast<int32_t>(b->jobs.size())) return set_error(NMFA_EINVAL, "one stream id per job");
+  std::lock_guard<std::mutex> g(b->mu);
+  int rc;
+  if ((rc = cuda_error(cudaSetDevice(b->device), "cudaSetDevice"))) return rc;
+  // the new descriptors replace the old ones after the last launch has finished
+  if ((rc = cuda_error(cudaStreamWaitEvent(b->own, b->done, 0), "stream wait"))) return rc;
+  for (size_t k = 0; k < b->plans.size(); ++k) {
+    std::vector<uint32_t> ids;
+    for (int32_t j : b->plan_jobs[k]) ids.push_back(stream_ids[j]);
+    tc_plan_set_streams(&b->plans[k], ids.data());
+    if ((rc = tc_upload_plan(b->plans[k], b->own))) return rc;
+  }
+  for (int32_t j = 0; j < count; ++j) b->jobs[j].stream_id = stream_ids[j];
+  return cuda_error(cudaEventRecord(b->done, b->own), "event record");
 }
 
 int nmfa_batch_sync(nmfa_batch* b) {

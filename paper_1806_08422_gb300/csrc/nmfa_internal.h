@@ -147,6 +147,7 @@ struct TcJob {
 };
 struct TcPlan {
   std::vector<unsigned char> host;   // group descriptors, items, per-CTA offsets
+  std::vector<int32_t> group_job;    // index (into the plan's jobs) of each group's job
   void* dev = nullptr;               // workspace base
   size_t groups_off = 0, items_off = 0, first_off = 0, flags_off = 0, flags_bytes = 0;
   int grid = 0;                      // CTAs launched
@@ -167,6 +168,9 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes);
 int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, int32_t* status, TcPlan* plan,
                   bool withhold_tile = false);
 int tc_upload_plan(const TcPlan& plan, cudaStream_t st);
+// Sets the noise stream id of every group of the plan's job j to stream_ids[j] (host
+// copy of the descriptors; upload it before the next launch).
+void tc_plan_set_streams(TcPlan* plan, const uint32_t* stream_ids);
 int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st);
 int launch_tc(const TcProblem& pb, const RunParams& rp, const TcWorkspace& ws,
               cudaStream_t st);

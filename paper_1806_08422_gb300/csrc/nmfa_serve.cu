@@ -13,7 +13,10 @@
 //     different launches overlaps;
 //   - on completion reads the energies, and either finishes the request (target
 //     met: time-to-target = completion - arrival) or reruns it with the next noise
-//     stream id, up to `max_attempts` runs; finished requests release their memory.
+//     stream id, up to `max_attempts` runs; finished requests release their memory;
+//   - a launch whose requests all rerun, and are launched again together, reuses its
+//     batch (plan and workspace) with the next noise stream ids instead of planning
+//     a new one.
 // Results depend only on each request (instance, schedule, seed, attempt), never on
 // what it was batched with: batches are bit-identical to solo runs.
 #include <cuda_runtime.h>
@@ -63,6 +66,12 @@ struct InFlight {
   cudaEvent_t ev = nullptr;
 };
 
+// A finished launch whose requests all rerun: its batch, kept for their next launch.
+struct Reusable {
+  nmfa_batch* batch = nullptr;
+  std::vector<Request*> reqs;  // in the batch's job order
+};
+
 }  // namespace
 
 struct nmfa_server {
@@ -84,7 +93,9 @@ struct nmfa_server {
   std::vector<cudaStream_t> streams;
   std::vector<bool> slot_busy;
   std::atomic<int64_t> launches{0};
+  std::atomic<int64_t> reused{0};  // launches that reused a batch
   int32_t max_batch = 0;          // most requests one launch has carried
+  std::vector<Reusable> reusable;  // worker thread only
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -197,30 +208,10 @@ void loader_main(nmfa_server* s) {
   }
 }
 
-int launch_batch(nmfa_server* s, std::vector<Request*>& reqs, int slot, InFlight* out) {
-  std::vector<nmfa_problem*> probs;
-  std::vector<nmfa_job> jobs;
-  for (Request* r : reqs) {
-    nmfa_job j{};
-    j.T_dev = r->T_dev;
-    j.t_f = r->t_f;
-    j.sigma = r->sigma;
-    j.alpha = r->alpha;
-    j.replicas = r->replicas;
-    j.seed = r->seed;
-    j.stream_id = static_cast<uint32_t>(r->res.attempts);  // attempt k draws noise stream k
-    j.signs_dev = r->signs_dev;
-    j.energy_dev = r->energy_dev;
-    probs.push_back(r->prob);
-    jobs.push_back(j);
-  }
-  nmfa_batch* b = nullptr;
-  int rc = nmfa_batch_create(probs.data(), jobs.data(), static_cast<int32_t>(jobs.size()), 0, &b);
-  if (rc) return rc;
-  if ((rc = nmfa_batch_launch(b, s->streams[slot]))) {
-    nmfa_batch_destroy(b);
-    return rc;
-  }
+// Launches batch b (jobs in the order of reqs) on the slot's stream.
+int launch_created(nmfa_server* s, nmfa_batch* b, const std::vector<Request*>& reqs, int slot, InFlight* out) {
+  int rc;
+  if ((rc = nmfa_batch_launch(b, s->streams[slot]))) return rc;
   cudaEvent_t ev = nullptr;
   cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   cudaEventRecord(ev, s->streams[slot]);
@@ -243,8 +234,67 @@ int launch_batch(nmfa_server* s, std::vector<Request*>& reqs, int slot, InFlight
   return NMFA_OK;
 }
 
+// Reuses a kept batch whose requests are exactly `take` (in any order): its jobs get
+// the requests' next noise streams.  Kept batches that do not match are released.
+bool launch_reused(nmfa_server* s, const std::vector<Request*>& take, int slot, InFlight* out) {
+  std::vector<Request*> want(take);
+  std::sort(want.begin(), want.end());
+  bool done = false;
+  for (Reusable& k : s->reusable) {
+    std::vector<Request*> have(k.reqs);
+    std::sort(have.begin(), have.end());
+    if (!done && have == want) {
+      std::vector<uint32_t> ids;
+      for (Request* r : k.reqs) ids.push_back(static_cast<uint32_t>(r->res.attempts));  // attempt k: stream k
+      if (nmfa_batch_set_stream_ids(k.batch, ids.data(), static_cast<int32_t>(ids.size())) == NMFA_OK &&
+          launch_created(s, k.batch, k.reqs, slot, out) == NMFA_OK) {
+        s->reused += 1;
+        k.batch = nullptr;
+        done = true;
+        continue;
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (Reusable& k : s->reusable)
+      if (k.batch) s->dead_batches.push_back(k.batch);
+    s->cv.notify_all();
+  }
+  s->reusable.clear();
+  return done;
+}
+
+int launch_batch(nmfa_server* s, std::vector<Request*>& reqs, int slot, InFlight* out) {
+  std::vector<nmfa_problem*> probs;
+  std::vector<nmfa_job> jobs;
+  for (Request* r : reqs) {
+    nmfa_job j{};
+    j.T_dev = r->T_dev;
+    j.t_f = r->t_f;
+    j.sigma = r->sigma;
+    j.alpha = r->alpha;
+    j.replicas = r->replicas;
+    j.seed = r->seed;
+    j.stream_id = static_cast<uint32_t>(r->res.attempts);  // attempt k draws noise stream k
+    j.signs_dev = r->signs_dev;
+    j.energy_dev = r->energy_dev;
+    probs.push_back(r->prob);
+    jobs.push_back(j);
+  }
+  nmfa_batch* b = nullptr;
+  int rc = nmfa_batch_create(probs.data(), jobs.data(), static_cast<int32_t>(jobs.size()), 0, &b);
+  if (rc) return rc;
+  if ((rc = launch_created(s, b, reqs, slot, out))) {
+    nmfa_batch_destroy(b);
+    return rc;
+  }
+  return NMFA_OK;
+}
+
 void complete(nmfa_server* s, InFlight& f) {
   const int rc = nmfa_batch_sync(f.batch);
+  bool all_rerun = rc == NMFA_OK;
   for (Request* r : f.reqs) {
     if (rc != NMFA_OK) {
       finish(s, r, rc);
@@ -264,9 +314,11 @@ void complete(nmfa_server* s, InFlight& f) {
     if (e <= r->target) {
       r->res.success = 1;
       r->res.time_to_target = s->now() - r->res.t_submit;
+      all_rerun = false;
       finish(s, r, NMFA_OK);
     } else if (r->res.attempts >= s->cfg.max_attempts) {
       r->res.time_to_target = -1.0;
+      all_rerun = false;
       finish(s, r, NMFA_OK);
     } else {
       std::lock_guard<std::mutex> g(s->mu);
@@ -274,7 +326,9 @@ void complete(nmfa_server* s, InFlight& f) {
       s->ready.push_front(r);  // reruns go first
     }
   }
-  {
+  if (all_rerun) {
+    s->reusable.push_back(Reusable{f.batch, f.reqs});  // for their next launch
+  } else {
     std::lock_guard<std::mutex> g(s->mu);
     s->dead_batches.push_back(f.batch);  // its workspace is released by the reaper
     s->cv.notify_all();
@@ -321,7 +375,7 @@ void worker_main(nmfa_server* s) {
       }
     }
     InFlight f;
-    const int rc = launch_batch(s, take, slot, &f);
+    const int rc = launch_reused(s, take, slot, &f) ? NMFA_OK : launch_batch(s, take, slot, &f);
     if (rc != NMFA_OK) {
       for (Request* r : take) finish(s, r, rc);
       continue;
@@ -416,9 +470,10 @@ int nmfa_server_drain(nmfa_server* s, double timeout_s) {
 }
 
 int nmfa_server_stats(nmfa_server* s, int64_t* launches, int64_t* mem_used, int32_t* outstanding,
-                      int32_t* max_requests_per_launch) {
+                      int32_t* max_requests_per_launch, int64_t* batches_reused) {
   if (s == nullptr) return set_error(NMFA_EINVAL, "NULL server");
   std::lock_guard<std::mutex> g(s->mu);
+  if (batches_reused) *batches_reused = s->reused.load();
   if (max_requests_per_launch) *max_requests_per_launch = s->max_batch;
   if (launches) *launches = s->launches.load();
   if (mem_used) *mem_used = s->mem_used;
@@ -436,6 +491,9 @@ void nmfa_server_destroy(nmfa_server* s) {
   if (s->loader.joinable()) s->loader.join();
   if (s->worker.joinable()) s->worker.join();
   if (s->reaper.joinable()) s->reaper.join();
+  for (Reusable& k : s->reusable)
+    if (k.batch) nmfa_batch_destroy(k.batch);
+  for (nmfa_batch* b : s->dead_batches) nmfa_batch_destroy(b);
   for (auto& kv : s->all) {
     Request* r = kv.second;
     if (r->prob) nmfa_destroy(r->prob);

@@ -52,7 +52,8 @@ SIGNATURES = {
     "nmfa_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(_u64)]),
     "nmfa_server_poll": (ctypes.c_int, [_P, _u64, _P, _P]),
     "nmfa_server_drain": (ctypes.c_int, [_P, _f64]),
-    "nmfa_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nmfa_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "nmfa_batch_set_stream_ids": (ctypes.c_int, [_P, _P, _i32]),
     "nmfa_server_destroy": (None, [_P]),
     "nmfa_debug_run": (ctypes.c_int, [_P, _P, _i32, _f64, _f64, _i32, _u64, _u32, _i32, _P, _P, _P, _P, _P,
                                       _P, _P]),
@@ -255,6 +256,11 @@ def nmfa_batch_sync(batch):
     _check(load().nmfa_batch_sync(batch))
 
 
+def nmfa_batch_set_stream_ids(batch, stream_ids):
+    ids = (ctypes.c_uint32 * len(stream_ids))(*[int(x) for x in stream_ids])
+    _check(load().nmfa_batch_set_stream_ids(batch, ids, len(stream_ids)))
+
+
 def nmfa_batch_info(batch):
     g, n, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().nmfa_batch_info(batch, ctypes.byref(g), ctypes.byref(n), ctypes.byref(b)))
@@ -333,9 +339,11 @@ def nmfa_server_drain(server, timeout_s=600.0):
 
 
 def nmfa_server_stats(server):
-    la, mu, out, mb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
-    _check(load().nmfa_server_stats(server, ctypes.byref(la), ctypes.byref(mu), ctypes.byref(out), ctypes.byref(mb)))
-    return {"launches": la.value, "mem_used": mu.value, "outstanding": out.value, "max_requests_per_launch": mb.value}
+    la, mu, out, mb, ru = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().nmfa_server_stats(server, ctypes.byref(la), ctypes.byref(mu), ctypes.byref(out), ctypes.byref(mb),
+                                    ctypes.byref(ru)))
+    return {"launches": la.value, "mem_used": mu.value, "outstanding": out.value, "max_requests_per_launch": mb.value,
+            "batches_reused": ru.value}
 
 
 def nmfa_server_destroy(server):

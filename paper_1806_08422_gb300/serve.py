@@ -84,7 +84,7 @@ def run_server(reqs, pool, t_f=1000, precision="bf16", max_inflight=2, max_attem
     spin = sum(x["spin_updates"] for x in res)
     return {"requests": len(res), "succeeded": len(ttt), "p50_ttt_s": percentile(ttt, 50),
             "p99_ttt_s": percentile(ttt, 99), "spin_updates_per_s": spin / wall, "wall_s": wall,
-            "launches": stats["launches"], "mean_attempts": float(np.mean([x["attempts"] for x in res])),
+            "launches": stats["launches"], "batches_reused": stats["batches_reused"], "mean_attempts": float(np.mean([x["attempts"] for x in res])),
             "errors": sum(1 for x in res if x["state"] < 0)}
 
 

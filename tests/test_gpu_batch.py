@@ -289,6 +289,34 @@ def test_forced_256_replica_tiles_match_128_replica_tiles(n, R, storage):
     p.close()
 
 
+@pytest.mark.parametrize("options", [0, 1])
+def test_set_stream_ids_reruns_with_fresh_noise(options):
+    # A created batch is re-targeted at other noise streams (plan and workspace kept,
+    # descriptors uploaded again): each execution equals the solo runs on the streams
+    # it was given, for jobs on different tile widths, with and without a CUDA graph.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    problems = [nmfa.Problem(inst.sk(300, 61), precision="bf16"), nmfa.Problem(inst.sk(2000, 62), precision="bf16")]
+    T = torch.as_tensor(inst.schedule(50), device=dev)
+    specs = [(T, 64, 21, 0), (T, 512, 22, 0)]
+    b, outs = _batch(problems, specs, options)
+    assert len(nmfa.nmfa_batch_plan(b)) == 2
+    for ids in ([0, 0], [1, 2], [2, 1]):
+        if ids != [0, 0]:
+            nmfa.nmfa_batch_set_stream_ids(b, ids)
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        for p, (Td, R, seed, _), sid, (s, e) in zip(problems, specs, ids, outs):
+            sa, ea = _alone(p, Td, R, seed, sid)
+            np.testing.assert_array_equal(s.cpu().numpy(), sa)
+            np.testing.assert_array_equal(e.cpu().numpy(), ea)
+    with pytest.raises(RuntimeError):
+        nmfa.nmfa_batch_set_stream_ids(b, [1])
+    nmfa.nmfa_batch_destroy(b)
+    for p in problems:
+        p.close()
+
+
 # --------------------------------------------------------------------------
 # CTA pairs (NMFA_BATCH_PAIR128): 128-replica tiles of problems whose row blocks pair
 # up run as clusters of two CTAs sharing one cta_group::2 MMA (M = 256).  Every tile

@@ -111,3 +111,23 @@ def test_request_arriving_mid_launch_starts_before_that_launch_ends():
     st = nmfa.nmfa_server_stats(srv)
     assert st["launches"] < 5 and st["max_requests_per_launch"] >= 2, st
     nmfa.nmfa_server_destroy(srv)
+
+
+def test_reruns_reuse_their_batch():
+    # A request that misses its target reruns on the next noise stream; alone on the
+    # server its reruns reuse the batch of its first attempt (no new plan), and its
+    # best energy is the best of the solo runs on streams 0, 1, 2.
+    from paper_1806_08422_gb300 import nmfa
+    J, T = inst.sk(400, 14), inst.schedule(120)
+    srv = nmfa.nmfa_server_create(0, 1, 3)
+    t = nmfa.nmfa_server_submit(srv, J, T, 128, -1e18, seed=7)
+    nmfa.nmfa_server_drain(srv, 300.0)
+    res = nmfa.nmfa_server_poll(srv, t, n=400)
+    assert res["state"] == 3 and res["error"] == 0 and res["attempts"] == 3 and res["success"] == 0
+    st = nmfa.nmfa_server_stats(srv)
+    assert st["launches"] == 3 and st["batches_reused"] == 2, st
+    solo = [_solo_best(J, T, 128, 7, a) for a in range(3)]
+    k = min(range(3), key=lambda a: solo[a][0])
+    assert res["best_energy"] == solo[k][0]
+    np.testing.assert_array_equal(res["best_signs"], solo[k][1])
+    nmfa.nmfa_server_destroy(srv)
