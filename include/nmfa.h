@@ -60,8 +60,8 @@ typedef enum {
                          half the bytes): the tensor kernel widens each staged slice to
                          BF16 in shared memory, so runs are bit-identical to NMFA_BF16
                          runs of the same J; the conversion costs time where J fits
-                         in L2 (about 1.2x the step time with 256-replica tiles, 2x
-                         with 128-replica tiles, measured on GB300) */
+                         in L2 (about 1.2x the step time with 256-replica tiles,
+                         1.5x with 128-replica tiles, measured on GB300) */
 } nmfa_precision;
 
 typedef struct nmfa_problem nmfa_problem; /* opaque; owns device copies of (h, J) */

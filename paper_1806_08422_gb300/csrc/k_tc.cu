@@ -98,16 +98,20 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   the byte order (k0, k2, k1, k3) within each 4-value group); its slices go by TMA
 //   into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes) and are written as
 //   BF16 into the slot's A operand (the MMA stays kind::f16 with both operands BF16)
-//   by two converter warps, half of each slice each (a third would put six warps on
-//   one scheduler, whose register file then allows 80 registers a thread instead of
-//   96); the slot's full barrier then also waits for both converter warps.
+//   by converter warps, each taking its share of every slice: eight for 128-replica
+//   tiles (whose 8 epilogue warps then cover 64 columns each), two for 256-replica
+//   tiles (beside their 16 epilogue warps; more would put six warps on one
+//   scheduler, whose register file then allows 80 registers a thread instead of 96);
+//   the slot's full barrier then also waits for every converter warp.
 template <int BN, bool PAIR = false, bool F8 = false>
 struct TcShape {
   static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
-  static constexpr int kColsPerWarp = BN == 256 ? 64 : 32;
-  static constexpr int kEpiWarps = BN == 256 ? 16 : BN / 8;
+  // epilogue warps of 64 columns for 256-replica tiles, and for FP8 128-replica tiles
+  // (8 warps, leaving room for 8 converter warps); of 32 columns otherwise
+  static constexpr int kColsPerWarp = (BN == 256 || (F8 && BN == 128)) ? 64 : 32;
+  static constexpr int kEpiWarps = 4 * BN / kColsPerWarp;
   static constexpr int kSubs = (BN == 64 && !PAIR) ? 2 : 1;  // tile pipelines per CTA
-  static constexpr int kConvWarps = F8 ? 2 : 0;                 // FP8 -> BF16 converter warps
+  static constexpr int kConvWarps = F8 ? (BN == 128 ? 8 : 2) : 0;  // FP8 -> BF16 converter warps
   static constexpr int kSubWarps = 2 + kEpiWarps + kConvWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
   static constexpr int kBRows = PAIR ? BN / 2 : BN;  // replica rows of each B slice in this CTA
@@ -357,14 +361,14 @@ __device__ __forceinline__ void arrive_bias(SharedCtl* ctl, uint32_t g, bool rem
 // will use (the Gaussian draws do not depend on the state, so with two accumulators
 // this runs while the tensor core still computes the previous step), then signalled
 // to the MMA issuer.
-template <int BN>
+template <int BN, bool F8 = false>
 __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base, int col0, int rbase, int i,
                                            uint32_t stream, const RoundKeys& rk, float sigma_ns, float dd, float hi,
                                            int lane, SharedCtl* ctl, bool remote) {
-  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
+  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN, false, F8>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll 1
-  for (int cc = 0; cc < TcShape<BN>::kColsPerWarp; cc += 16) {
+  for (int cc = 0; cc < TcShape<BN, false, F8>::kColsPerWarp; cc += 16) {
 #pragma unroll
     for (int gq = 0; gq < 4; ++gq) {
       const int r4 = rbase + cc + 4 * gq;
@@ -384,15 +388,15 @@ __device__ __forceinline__ void write_bias(int t, uint32_t g, uint32_t lane_base
 }
 
 // (A') the accumulator start of the energy product: 2 h_i, no noise.
-template <int BN>
+template <int BN, bool F8 = false>
 __device__ __forceinline__ void write_energy_bias(uint32_t g, uint32_t lane_base, int col0, float hi, int lane,
                                                   SharedCtl* ctl, bool remote) {
-  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN>::kColAcc1 : 0u);
+  const uint32_t acc = lane_base + ((g & 1u) ? TcShape<BN, false, F8>::kColAcc1 : 0u);
   uint32_t v[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __float_as_uint(2.0f * hi);
 #pragma unroll 1
-  for (int cc = 0; cc < TcShape<BN>::kColsPerWarp; cc += 16) ptx::tmem_st16(acc + col0 + cc, v);
+  for (int cc = 0; cc < TcShape<BN, false, F8>::kColsPerWarp; cc += 16) ptx::tmem_st16(acc + col0 + cc, v);
   ptx::tmem_wait_st();
   ptx::tc_fence_before();
   __syncwarp();
@@ -470,13 +474,14 @@ __device__ __noinline__ void energy_readout(const TcGroup* __restrict__ g, uint3
 // q = (e + QOFF) % 4 (spins 32q..32q+31 of the tile); it serves that quarter and
 // column group e / 4 (32 replicas), 16 columns per tcgen05.ld.  `gstep` counts the CTA's steps across items
 // (the parity of the accumulator barriers).  Returns false on abort.
-template <int BN, int QOFF, bool PAIR>
+template <int BN, int QOFF, bool PAIR, bool F8 = false>
 __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int b, int e, int lane, uint32_t tmem,
                                               SharedCtl* ctl, int32_t* status, uint32_t& gstep, uint32_t crank) {
   const bool remote_bias = PAIR && crank != 0u;
-  constexpr int kCW = TcShape<BN>::kColsPerWarp;
-  constexpr bool kDouble = TcShape<BN>::kDoubleAcc;
-  constexpr uint32_t kColAcc1 = TcShape<BN>::kColAcc1, kColMaster = TcShape<BN>::kColMaster;
+  using Shape = TcShape<BN, false, F8>;
+  constexpr int kCW = Shape::kColsPerWarp;
+  constexpr bool kDouble = Shape::kDoubleAcc;
+  constexpr uint32_t kColAcc1 = Shape::kColAcc1, kColMaster = Shape::kColMaster;
   const int q = (e + QOFF) & 3;
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
   const int n = g->n, n_pad = g->n_pad, t_f = g->t_f, R = g->replicas;
@@ -528,7 +533,7 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
   // (A) the bias of step t: the Gaussian draws do not depend on the state, so they
   // are generated while the tensor core still computes the previous step
   if (t_f > 0)
-    write_bias<BN>(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl, remote_bias);
+    write_bias<BN, F8>(0, gstep, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl, remote_bias);
 
   for (int t = 0; t < t_f; ++t, ++gstep) {
     float inv_T = 0.0f;
@@ -538,10 +543,10 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
     // the next step's bias goes into the other accumulator (read last two steps ago)
     if constexpr (kDouble) {
       if (t + 1 < t_f)
-        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
+        write_bias<BN, F8>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
                        remote_bias);
       else if (energy_pass)
-        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
+        write_energy_bias<BN, F8>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
     }
     // (B) the update, once the product is in TMEM
     if (!__all_sync(0xffffffffu, wait_bar(ptx::smem_u32(&ctl->acc_full), gstep & 1u, ctl, status))) return false;
@@ -603,10 +608,10 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
       // one accumulator: the next step's bias goes in once this step's product has
       // been read (the draws then overlap the other tiles' publication and the copies)
       if (t + 1 < t_f)
-        write_bias<BN>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
+        write_bias<BN, F8>(t + 1, gstep + 1, lane_base, col0, rbase, i, stream, rk, sigma_ns, dd, hi, lane, ctl,
                        remote_bias);
       else if (energy_pass)
-        write_energy_bias<BN>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
+        write_energy_bias<BN, F8>(gstep + 1, lane_base, col0, hi, lane, ctl, remote_bias);
     }
   }
   // sign readout of Algorithm 1: sign of the FP32 master state, zero reads as +1
@@ -941,7 +946,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       const TcItem item = items[w];
       const TcGroup* g = groups + item.group;
       const int b = PAIR ? 2 * item.b + static_cast<int>(crank) : item.b;
-      ok = epilogue_item<BN, (2 + SUB * kSubWarps) & 3, PAIR>(g, b, e, lane, tmem, &ctl, status, gstep, crank);
+      ok = epilogue_item<BN, (2 + SUB * kSubWarps) & 3, PAIR, F8>(g, b, e, lane, tmem, &ctl, status, gstep, crank);
     }
   }
 }
@@ -1438,13 +1443,11 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   return NMFA_OK;
 }
 
-// FP8-stored couplings take one-CTA 128- or 256-replica tiles (two converter warps
-// beside a pipeline's 18; the 64-replica CTA's two pipelines leave no room), the
-// BF16 widths except 128 where BF16 would take 64.  Results do not depend on the
-// width.  256-replica tiles convert each J slice
-// once for twice the replicas, but on half the SMs: SK runs of 200 steps, us per step
-// with 256- against 128-replica tiles: n = 4096, R = 512: 38.5 / 34.2; n = 2000,
-// R = 1024: 23.2 / 18.7; n = 512, R = 1024: 12.1 / 7.0.
+// FP8-stored couplings take one-CTA 128- or 256-replica tiles (the 64-replica CTA's
+// two pipelines leave no room for converter warps): the BF16 widths, except 128
+// where BF16 would take 64.  256-replica tiles convert each J slice once for twice
+// the replicas but run on half the SMs, and measure slower wherever 128-replica tiles
+// fit in one wave.  Results do not depend on the width.
 int tc_pick_bn_for(const TcProblem& pb, int32_t replicas) {
   const int bn = tc_pick_bn(replicas, pb.n_pad);
   return (pb.fp8 && bn == 64) ? 128 : bn;
