@@ -60,7 +60,7 @@ typedef enum {
                          half the bytes): the tensor kernel widens each staged slice to
                          BF16 in shared memory, so runs are bit-identical to NMFA_BF16
                          runs of the same J; the conversion costs time where J fits
-                         in L2 (about 1.2x the step time with 256-replica tiles,
+                         in L2 (about 1.1x the step time with 256-replica tiles,
                          1.5x with 128-replica tiles, measured on GB300) */
 } nmfa_precision;
 

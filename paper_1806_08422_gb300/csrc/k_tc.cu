@@ -98,20 +98,21 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   the byte order (k0, k2, k1, k3) within each 4-value group); its slices go by TMA
 //   into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes) and are written as
 //   BF16 into the slot's A operand (the MMA stays kind::f16 with both operands BF16)
-//   by converter warps, each taking its share of every slice: eight for 128-replica
-//   tiles (whose 8 epilogue warps then cover 64 columns each), two for 256-replica
-//   tiles (beside their 16 epilogue warps; more would put six warps on one
-//   scheduler, whose register file then allows 80 registers a thread instead of 96);
-//   the slot's full barrier then also waits for every converter warp.
+//   by eight converter warps, one 16-row part of every slice each (the tile's 8
+//   epilogue warps then cover twice the columns of the BF16 form: more warps would
+//   put six on one scheduler, whose register file then allows 80 registers a thread
+//   instead of 96); the slot's full barrier then also waits for every converter
+//   warp.
 template <int BN, bool PAIR = false, bool F8 = false>
 struct TcShape {
   static constexpr bool kDoubleAcc = BN != 256;     // two accumulators (bias written ahead)
-  // epilogue warps of 64 columns for 256-replica tiles, and for FP8 128-replica tiles
-  // (8 warps, leaving room for 8 converter warps); of 32 columns otherwise
-  static constexpr int kColsPerWarp = (BN == 256 || (F8 && BN == 128)) ? 64 : 32;
+  // epilogue warps of 32 columns (64- and 128-replica tiles) or 64 (256-replica
+  // tiles); with FP8 couplings twice as wide (8 warps), leaving room for 8 converter
+  // warps in the same 18 warps and 96 registers a thread
+  static constexpr int kColsPerWarp = (F8 && BN == 256) ? 128 : (BN == 256 || (F8 && BN == 128)) ? 64 : 32;
   static constexpr int kEpiWarps = 4 * BN / kColsPerWarp;
   static constexpr int kSubs = (BN == 64 && !PAIR) ? 2 : 1;  // tile pipelines per CTA
-  static constexpr int kConvWarps = F8 ? (BN == 128 ? 8 : 2) : 0;  // FP8 -> BF16 converter warps
+  static constexpr int kConvWarps = F8 ? 8 : 0;  // FP8 -> BF16 converter warps
   static constexpr int kSubWarps = 2 + kEpiWarps + kConvWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
   static constexpr int kBRows = PAIR ? BN / 2 : BN;  // replica rows of each B slice in this CTA
