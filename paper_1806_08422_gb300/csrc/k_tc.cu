@@ -94,7 +94,7 @@ constexpr uint32_t kABytes = kBM * 128;  // one A (J) atom: 128 rows x 128 bytes
 //   lands 48 KB of operands per 128-deep K slice instead of 64 KB, and the tensor
 //   core reads 96 instead of 128 bytes per clock from each SM's shared memory (at
 //   the full MMA rate).  Ring of 4 slots of 48 KB; the even CTA issues the MMAs.
-//   FP8 (F8 = true, 128 or 256 replicas, one CTA per tile): J is stored in E4M3 (in
+//   FP8 (F8 = true, 64, 128 or 256 replicas, one CTA per tile): J is stored in E4M3 (in
 //   the byte order (k0, k2, k1, k3) within each 4-value group); its slices go by TMA
 //   into a 2-buffer staging ring of 16 KB (128 rows x 128 K bytes) and are written as
 //   BF16 into the slot's A operand (the MMA stays kind::f16 with both operands BF16)
@@ -111,12 +111,13 @@ struct TcShape {
   // warps in the same 18 warps and 96 registers a thread
   static constexpr int kColsPerWarp = (F8 && BN == 256) ? 128 : (BN == 256 || (F8 && BN == 128)) ? 64 : 32;
   static constexpr int kEpiWarps = 4 * BN / kColsPerWarp;
-  static constexpr int kSubs = (BN == 64 && !PAIR) ? 2 : 1;  // tile pipelines per CTA
+  static constexpr int kSubs = (BN == 64 && !PAIR && !F8) ? 2 : 1;  // tile pipelines per CTA
   static constexpr int kConvWarps = F8 ? 8 : 0;  // FP8 -> BF16 converter warps
   static constexpr int kSubWarps = 2 + kEpiWarps + kConvWarps;  // warps per pipeline
   static constexpr int kThreads = 32 * kSubWarps * kSubs;
   static constexpr int kBRows = PAIR ? BN / 2 : BN;  // replica rows of each B slice in this CTA
-  static constexpr int kStages = PAIR ? 4 : (BN == 128 ? 3 : 2);  // ring slots per pipeline
+  // ring slots per pipeline (the FP8 64-replica CTA has one pipeline, room for four)
+  static constexpr int kStages = PAIR ? 4 : (BN == 128 ? 3 : ((BN == 64 && F8) ? 4 : 2));
   static constexpr uint32_t kBAtomBytes = kBRows * 128;  // one B (S) atom: kBRows rows x 128 bytes
   static constexpr uint32_t kStageBytes = kAtoms * (kABytes + kBAtomBytes);
   static constexpr int kMmaM = PAIR ? 2 * kBM : kBM;
@@ -134,7 +135,7 @@ struct TcShape {
   static_assert(kEpiWarps * kColsPerWarp == 4 * BN, "every (quarter, column) pair once");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
   static_assert(!PAIR || BN == 128, "CTA pairs take 128-replica tiles");
-  static_assert(!F8 || (!PAIR && BN != 64), "FP8 couplings take one-CTA 128- or 256-replica tiles");
+  static_assert(!F8 || !PAIR, "FP8 couplings take one-CTA tiles");
 };
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 // A pipeline that reaches a new group early waits for the group's other pipelines to
@@ -1136,19 +1137,22 @@ int co_resident_units_t(int* capacity) {
 }
 int co_resident_units(int bn, bool pair, bool f8, int* capacity) {
   if (pair) return co_resident_units_t<128, true, false>(capacity);
-  if (f8) return bn == 256 ? co_resident_units_t<256, false, true>(capacity) : co_resident_units_t<128, false, true>(capacity);
+  if (f8)
+    return bn == 256  ? co_resident_units_t<256, false, true>(capacity)
+           : bn == 64 ? co_resident_units_t<64, false, true>(capacity)
+                      : co_resident_units_t<128, false, true>(capacity);
   return bn == 64 ? co_resident_units_t<64, false, false>(capacity)
                   : bn == 256 ? co_resident_units_t<256, false, false>(capacity)
                               : co_resident_units_t<128, false, false>(capacity);
 }
 // Tile pipelines per scheduling unit.
-int tc_subs(int bn, bool pair) { return (bn == 64 && !pair) ? TcShape<64>::kSubs : 1; }
+int tc_subs(int bn, bool pair, bool f8) { return (bn == 64 && !pair && !f8) ? TcShape<64>::kSubs : 1; }
 // Work-list slots of the co-resident grid: tile pipelines, or CTA pairs.
 int co_resident_slots(int bn, bool pair, bool f8, int* slots) {
   int units = 0;
   const int rc = co_resident_units(bn, pair, f8, &units);
   if (rc) return rc;
-  *slots = units * tc_subs(bn, pair);
+  *slots = units * tc_subs(bn, pair, f8);
   return NMFA_OK;
 }
 
@@ -1223,7 +1227,7 @@ int tc_plan_bytes(const TcJob* jobs, int32_t count, int64_t* bytes) {
     const int nb = jobs[j].pb.n_pad / kBM;
     if (bn != jobs[0].bn || jobs[j].pair != pair || jobs[j].pb.fp8 != f8)
       return set_error(NMFA_EINVAL, "one plan takes one tile variant");
-    if (f8 && (pair || bn == 64)) return set_error(NMFA_EINVAL, "FP8 couplings take one-CTA 128- or 256-replica tiles");
+    if (f8 && pair) return set_error(NMFA_EINVAL, "FP8 couplings take one-CTA tiles");
     if (pair && nb % 2 != 0) return set_error(NMFA_EINVAL, "CTA pairs need an even number of row blocks");
     const int units = pair ? nb / 2 : nb;
     if (units > capacity)
@@ -1249,7 +1253,7 @@ int tc_build_plan(const TcJob* jobs, int32_t count, void* ws, int64_t ws_bytes, 
   int ctas = 0;  // scheduling units: CTAs, or CTA pairs
   int rc = co_resident_units(jobs[0].bn, pair, f8, &ctas);
   if (rc) return rc;
-  const int subs = tc_subs(jobs[0].bn, pair);
+  const int subs = tc_subs(jobs[0].bn, pair, f8);
   // scheduler slot s is pipeline s / ctas of unit s % ctas: every unit's first
   // pipeline fills before any second one
   const int capacity = ctas * subs;
@@ -1403,14 +1407,17 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
     return rc;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.grid, 1, 1);
-  cfg.blockDim = dim3(plan.f8 ? (plan.bn == 256 ? TcShape<256, false, true>::kThreads : TcShape<128, false, true>::kThreads)
+  cfg.blockDim = dim3(plan.f8 ? (plan.bn == 256  ? TcShape<256, false, true>::kThreads
+                                 : plan.bn == 64 ? TcShape<64, false, true>::kThreads
+                                                 : TcShape<128, false, true>::kThreads)
                       : plan.pair      ? TcShape<128, true>::kThreads
                       : plan.bn == 64  ? TcShape<64>::kThreads
                       : plan.bn == 256 ? TcShape<256>::kThreads
                                        : TcShape<128>::kThreads,
                       1, 1);
-  cfg.dynamicSmemBytes = plan.f8 ? (plan.bn == 256 ? TcShape<256, false, true>::kSmemBytes
-                                                   : TcShape<128, false, true>::kSmemBytes)
+  cfg.dynamicSmemBytes = plan.f8 ? (plan.bn == 256  ? TcShape<256, false, true>::kSmemBytes
+                                     : plan.bn == 64 ? TcShape<64, false, true>::kSmemBytes
+                                                     : TcShape<128, false, true>::kSmemBytes)
                          : plan.pair      ? TcShape<128, true>::kSmemBytes
                          : plan.bn == 64  ? TcShape<64>::kSmemBytes
                          : plan.bn == 256 ? TcShape<256>::kSmemBytes
@@ -1431,10 +1438,12 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   const TcGroup* dg = reinterpret_cast<const TcGroup*>(d + plan.groups_off);
   const TcItem* di = reinterpret_cast<const TcItem*>(d + plan.items_off);
   const int32_t* df = reinterpret_cast<const int32_t*>(d + plan.first_off);
-  const cudaError_t ce = plan.f8 ? (plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256, false, true>, dg, di, df,
-                                                                      plan.status)
-                                                   : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, false, true>, dg, di, df,
-                                                                      plan.status))
+  const cudaError_t ce = plan.f8 ? (plan.bn == 256  ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256, false, true>, dg, di, df,
+                                                                       plan.status)
+                                     : plan.bn == 64 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64, false, true>, dg, di, df,
+                                                                       plan.status)
+                                                     : cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, false, true>, dg, di, df,
+                                                                       plan.status))
                          : plan.pair      ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<128, true>, dg, di, df, plan.status)
                          : plan.bn == 64  ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<64>, dg, di, df, plan.status)
                          : plan.bn == 256 ? cudaLaunchKernelEx(&cfg, nmfa_tc_kernel<256>, dg, di, df, plan.status)
@@ -1444,15 +1453,13 @@ int tc_enqueue_plan(const TcPlan& plan, bool upload, cudaStream_t st) {
   return NMFA_OK;
 }
 
-// FP8-stored couplings take one-CTA 128- or 256-replica tiles (the 64-replica CTA's
-// two pipelines leave no room for converter warps): the BF16 widths, except 128
-// where BF16 would take 64.  256-replica tiles convert each J slice once for twice
-// the replicas but run on half the SMs, and measure slower wherever 128-replica tiles
-// fit in one wave.  Results do not depend on the width.
-int tc_pick_bn_for(const TcProblem& pb, int32_t replicas) {
-  const int bn = tc_pick_bn(replicas, pb.n_pad);
-  return (pb.fp8 && bn == 64) ? 128 : bn;
-}
+// FP8-stored couplings take the BF16 widths.  Their 64-replica tiles run one
+// pipeline per CTA (the converter warps take the second pipeline's place), which
+// fits: 64 is picked only where the tiles fill at most the SMs.  256-replica tiles
+// convert each J slice once for twice the replicas but run on half the SMs, and
+// measure slower wherever 128-replica tiles fit in one wave.  Results do not depend
+// on the width.
+int tc_pick_bn_for(const TcProblem& pb, int32_t replicas) { return tc_pick_bn(replicas, pb.n_pad); }
 
 int tc_workspace_bytes(const TcProblem& pb, int32_t replicas, int64_t* bytes) {
   TcJob jb{};

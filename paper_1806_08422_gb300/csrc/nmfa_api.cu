@@ -314,16 +314,18 @@ struct HostCompact {
   int64_t ld8 = 0;
 };
 
-uint8_t e4m3_bits(double v) {  // v exactly representable, |v| <= 448
-  const uint8_t sign = std::signbit(v) ? 0x80 : 0x00;
-  const double a = std::fabs(v);
-  if (a == 0.0) return sign;
-  int e = 0;
-  const double fr = std::frexp(a, &e);  // a = (2 fr) * 2^(e - 1)
-  const int ex = e - 1;
-  if (ex < -6) return static_cast<uint8_t>(sign | static_cast<int>(std::ldexp(a, 9)));  // subnormal: k * 2^-9
-  const int mant = static_cast<int>((2.0 * fr - 1.0) * 8.0);
-  return static_cast<uint8_t>(sign | ((ex + 7) << 3) | mant);
+// v exactly representable in E4M3 (so also in binary32): the E4M3 fields are read off
+// the binary32 pattern (exponent rebiased from 127 to 7, the top 3 fraction bits);
+// below 2^-6 the value is k 2^-9 with k = 1..7 stored as the subnormal fraction.
+uint8_t e4m3_bits(double v) {
+  const float f = static_cast<float>(v);
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  const uint8_t sign = static_cast<uint8_t>((b >> 24) & 0x80u);
+  if ((b & 0x7FFFFFFFu) == 0u) return sign;
+  const int e = static_cast<int>((b >> 23) & 0xFFu) - 127;
+  if (e >= -6) return static_cast<uint8_t>(sign | ((e + 7) << 3) | ((b >> 20) & 7u));
+  return static_cast<uint8_t>(sign | static_cast<int>(std::fabs(f) * 512.0f));
 }
 
 uint16_t bf16_bits(double v) {  // v exactly representable in BF16
@@ -1071,7 +1073,6 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
            : (options & NMFA_BATCH_BN256) ? 256
            : ((options & NMFA_BATCH_AUTOTUNE) && p->precision == NMFA_BF16) ? nmfa_autotuned_bn(p, jb.replicas)
                                              : tc_pick_bn_for(t.pb, jb.replicas);
-    if (t.pb.fp8 && t.bn == 64) t.bn = 128;  // FP8 couplings take 128- or 256-replica tiles
     // CTA pairs only on request (where the problem allows them; not with FP8 couplings)
     t.pair = (options & NMFA_BATCH_PAIR128) && !t.pb.fp8 && tc_use_pair(t.bn, p->n_pad);
     b->bn.push_back(t.bn);
@@ -1082,7 +1083,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     bool pair, f8;
   };
   const Variant variants[] = {{256, false, false}, {256, false, true}, {128, true, false},
-                              {128, false, false}, {128, false, true}, {64, false, false}};
+                              {128, false, false}, {128, false, true}, {64, false, false}, {64, false, true}};
   for (const Variant& var : variants) {
     std::vector<TcJob> part;
     std::vector<int32_t> part_jobs;

@@ -159,7 +159,7 @@ struct TcPlan {
 };
 // Default replicas per tile (64, 128 or 256) of a run of `replicas` replicas of an n_pad problem.
 int tc_pick_bn(int32_t replicas, int32_t n_pad);
-// The same for this problem's storage (FP8-stored couplings take 128 for a pick of 64).
+// The same for this problem's storage (FP8-stored couplings take the same widths).
 int tc_pick_bn_for(const TcProblem& pb, int32_t replicas);
 // Whether 128-replica tiles of an n_pad problem run as CTA pairs (results do not change).
 bool tc_use_pair(int bn, int32_t n_pad);

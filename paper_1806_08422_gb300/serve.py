@@ -63,7 +63,7 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def run_server(reqs, pool, t_f=1000, precision="bf16", max_inflight=2, max_attempts=4, timeout_s=600.0):
+def run_server(reqs, pool, t_f=1000, precision="bf16_fp8j", max_inflight=2, max_attempts=4, timeout_s=600.0):
     T = inst.schedule(t_f)
     srv = nmfa.nmfa_server_create(0, max_inflight, max_attempts)
     tickets = []
@@ -130,7 +130,7 @@ def main():
     ap.add_argument("--n-hi", type=int, default=8192)
     ap.add_argument("--t-f", type=int, default=1000)
     ap.add_argument("--max-inflight", type=int, default=2)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16_fp8j"],
+    ap.add_argument("--precision", default="bf16_fp8j", choices=["bf16", "bf16_fp8j"],
                     help="storage of J: bf16, or bf16_fp8j (E4M3, half the bytes, converted in the kernel)")
     ap.add_argument("--fp32-cap", type=float, default=30.0, help="seconds of FP32 FIFO serving (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
