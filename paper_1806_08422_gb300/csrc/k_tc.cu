@@ -277,35 +277,37 @@ __device__ __forceinline__ bool wait_block(const uint32_t* f0, int nb, int k, ui
 // on the slot's full barrier (one arrival per converter warp each).
 constexpr uint32_t kConvParts = 8;
 
-// Rows 16 part .. 16 part + 15 of a staged slice -> BF16 atoms; lane l converts the
-// 16-byte chunks l, l + 32, l + 64, l + 96 of the part (row 16 part + l / 8 + 4 u,
-// K values 16 (l % 8) .. + 15), ILP chunks at a time.
+// Rows 16 part .. 16 part + 15 of a staged slice -> BF16 atoms.  A 16-byte access is
+// served 8 lanes at a time, so each group of 8 lanes takes one 16-value chunk c
+// (K values 16c .. 16c + 15) of 8 consecutive rows: their 8 row swizzles (r mod 8)
+// put both the loads and the stores of the group on 8 distinct 16-byte bank groups.
+// Lane l converts chunk l / 8 + 4 (u / 2) of row 16 part + l % 8 + 8 (u % 2),
+// u = 0 .. 3, ILP chunks at a time.
 template <int ILP>
 __device__ __forceinline__ void convert_part(uint32_t src, uint32_t dst, uint32_t part, int lane) {
-  const uint32_t c = static_cast<uint32_t>(lane & 7);
-  const uint32_t r0 = part * 16u + static_cast<uint32_t>(lane >> 3);
-  // atom c / 4 holds K 64 (c / 4) .. + 63; the chunk's 16 values fill chunks
-  // 2 (c % 4) and 2 (c % 4) + 1 of the row there
-  const uint32_t atom = dst + (c >> 2) * kABytes;
-  const uint32_t c0 = 2u * (c & 3u);
 #pragma unroll
   for (int u0 = 0; u0 < 4; u0 += ILP) {
     uint4 v[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      const uint32_t r = r0 + 4u * static_cast<uint32_t>(u0 + u);
+      const uint32_t r = part * 16u + static_cast<uint32_t>(lane & 7) + 8u * ((u0 + u) & 1);
+      const uint32_t c = static_cast<uint32_t>(lane >> 3) + 4u * ((u0 + u) >> 1);
       v[u] = ptx::ld_shared_v4(src + r * 128u + ((c ^ (r & 7u)) << 4));
     }
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      const uint32_t r = r0 + 4u * static_cast<uint32_t>(u0 + u);
+      const uint32_t r = part * 16u + static_cast<uint32_t>(lane & 7) + 8u * ((u0 + u) & 1);
+      const uint32_t c = static_cast<uint32_t>(lane >> 3) + 4u * ((u0 + u) >> 1);
       const uint32_t sw = r & 7u;
       uint4 lo, hi;  // BF16 values 16c .. 16c + 7 and 16c + 8 .. 16c + 15
       ptx::e4m3x4p_to_bf16x2x2(v[u].x, lo.x, lo.y);
       ptx::e4m3x4p_to_bf16x2x2(v[u].y, lo.z, lo.w);
       ptx::e4m3x4p_to_bf16x2x2(v[u].z, hi.x, hi.y);
       ptx::e4m3x4p_to_bf16x2x2(v[u].w, hi.z, hi.w);
-      const uint32_t row = atom + r * 128u;
+      // atom c / 4 holds K 64 (c / 4) .. + 63; the chunk's 16 values fill chunks
+      // 2 (c % 4) and 2 (c % 4) + 1 of row r there
+      const uint32_t row = dst + (c >> 2) * kABytes + r * 128u;
+      const uint32_t c0 = 2u * (c & 3u);
       ptx::st_shared_v4(row + ((c0 ^ sw) << 4), lo);
       ptx::st_shared_v4(row + (((c0 + 1u) ^ sw) << 4), hi);
     }
