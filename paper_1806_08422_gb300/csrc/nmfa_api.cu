@@ -957,6 +957,12 @@ struct nmfa_batch {
   std::vector<std::vector<int32_t>> plan_jobs;  // per plan: the batch index of each of its jobs
   cudaStream_t own = nullptr;
   cudaEvent_t done = nullptr;
+  // plans 1.. run beside plan 0 on their own streams when all their CTAs fit the
+  // GPU together (fork / join events); otherwise one after the other
+  bool concurrent = false;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int device = 0;
@@ -972,6 +978,9 @@ static void free_batch(nmfa_batch* b) {
   pool_free(b->signs.p);
   pool_free(b->status);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->side_done) cudaEventDestroy(e);
+  for (cudaStream_t x : b->side) cudaStreamDestroy(x);
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
 }
@@ -980,8 +989,23 @@ static void free_batch(nmfa_batch* b) {
 // per job) on `st`; the plan was uploaded at creation.
 static int batch_enqueue(nmfa_batch* b, cudaStream_t st) {
   int rc;
-  for (const TcPlan& plan : b->plans)
-    if ((rc = tc_enqueue_plan(plan, false, st))) return rc;
+  if (b->concurrent) {
+    // fork: plans 1.. on the side streams after everything before on `st`; join
+    // before the energy kernels
+    if ((rc = cuda_error(cudaEventRecord(b->fork, st), "fork"))) return rc;
+    for (size_t k = 1; k < b->plans.size(); ++k) {
+      cudaStream_t x = b->side[k - 1];
+      if ((rc = cuda_error(cudaStreamWaitEvent(x, b->fork, 0), "fork wait"))) return rc;
+      if ((rc = tc_enqueue_plan(b->plans[k], false, x))) return rc;
+      if ((rc = cuda_error(cudaEventRecord(b->side_done[k - 1], x), "join"))) return rc;
+    }
+    if ((rc = tc_enqueue_plan(b->plans[0], false, st))) return rc;
+    for (size_t k = 1; k < b->plans.size(); ++k)
+      if ((rc = cuda_error(cudaStreamWaitEvent(st, b->side_done[k - 1], 0), "join wait"))) return rc;
+  } else {
+    for (const TcPlan& plan : b->plans)
+      if ((rc = tc_enqueue_plan(plan, false, st))) return rc;
+  }
   for (size_t j = 0; j < b->jobs.size(); ++j) {
     const nmfa_job& jb = b->jobs[j];
     if (b->energy_fused[j] || (jb.energy_dev == nullptr && jb.energy_i64_dev == nullptr)) continue;
@@ -1110,6 +1134,26 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     if ((rc = tc_upload_plan(b->plans.back(), b->own))) return fail(rc);
   }
   if ((rc = cuda_error(cudaStreamSynchronize(b->own), "plan upload"))) return fail(rc);
+  if (b->plans.size() > 1) {
+    // Concurrent plans need all their CTAs resident at once (each CTA holds an SM's
+    // tensor memory): otherwise a later plan's groups could start partly and wait
+    // for the rest of their tiles until an earlier plan ends.
+    int sms = 0, total = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    for (const TcPlan& pl : b->plans) total += pl.grid;
+    if (sms > 0 && total <= sms) {
+      b->concurrent = true;
+      if ((rc = cuda_error(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event"))) return fail(rc);
+      for (size_t k = 1; k < b->plans.size(); ++k) {
+        b->side.emplace_back();
+        if ((rc = cuda_error(cudaStreamCreateWithFlags(&b->side.back(), cudaStreamNonBlocking), "stream")))
+          return fail(rc);
+        b->side_done.emplace_back();
+        if ((rc = cuda_error(cudaEventCreateWithFlags(&b->side_done.back(), cudaEventDisableTiming), "event")))
+          return fail(rc);
+      }
+    }
+  }
   if (options & NMFA_BATCH_GRAPH) {
     if ((rc = cuda_error(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "capture"))) return fail(rc);
     rc = batch_enqueue(b, b->own);
