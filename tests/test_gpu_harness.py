@@ -35,7 +35,7 @@ def test_tts_harness_success_probability_matches_oracle():
         p = float(np.mean(ev <= e0))
         assert lo <= p <= hi, (k, p, k_ref / samples, lo, hi)
         agree.append(float(np.mean((ev <= e0) == (ref <= e0))))
-    # pairing: most runs reach the same verdict on both sides
+    # pairing: most runs reach the same outcome on both sides
     assert np.mean(agree) > 0.9, agree
     # the harness's own summary with these targets: p per instance and TTS99 from tau
     res = tts.run_class("sk", n, samples, t_f, seed, targets=targets)
