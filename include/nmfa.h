@@ -139,8 +139,9 @@ int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
                     void* cuda_stream);
 
 /*
- * nmfa_run_device_noalloc -- nmfa_run_device for an NMFA_BF16 problem that allocates
- * nothing.  The paper has no counterpart; this exists for callers that cannot
+ * nmfa_run_device_noalloc -- nmfa_run_device for an NMFA_BF16 or NMFA_BF16_FP8J
+ * problem that allocates nothing (FP8-stored couplings are read as stored and
+ * widened in the kernel, so they need no scratch).  The paper has no counterpart; this exists for callers that cannot
  * allocate device memory while they run: code inside a CUDA stream capture (an
  * allocation there is not part of the graph and may synchronise the device), a
  * framework whose memory pool owns all device memory, or a serving loop that must

@@ -894,7 +894,8 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
                             int32_t replicas, uint64_t seed, uint32_t stream_id, int8_t* signs_dev,
                             double* energy_dev, int64_t* energy_i64_dev, void* cuda_stream) {
   if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
-  if (p->precision != NMFA_BF16) return set_error(NMFA_EUNSUPPORTED, "nmfa_run_device_noalloc takes NMFA_BF16 problems");
+  if (p->precision != NMFA_BF16 && p->precision != NMFA_BF16_FP8J)
+    return set_error(NMFA_EUNSUPPORTED, "nmfa_run_device_noalloc takes NMFA_BF16 or NMFA_BF16_FP8J problems");
   if (signs_dev == nullptr) return set_error(NMFA_EINVAL, "nmfa_run_device_noalloc needs a signs buffer");
   if (t_f < 0 || (t_f > 0 && T_dev == nullptr)) return set_error(NMFA_EINVAL, "bad t_f or T");
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) return set_error(NMFA_EINVAL, "sigma must be >= 0");
@@ -923,7 +924,7 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
   pb.n = p->n;
   pb.n_pad = p->n_pad;
   pb.Jq = p->Jq;
-  pb.fp8 = false;
+  pb.fp8 = p->precision == NMFA_BF16_FP8J;  // read as stored, widened in the kernel: no scratch for J
   pb.inv_d32 = p->inv_d32;
   pb.h32 = p->h32;
   pb.energy_exact = p->energy_exact;

@@ -32,12 +32,15 @@ def test_noalloc_matches_run_device_on_consecutive_calls():
     __graft_entry__.build()
     dev = torch.device("cuda", 0)
     # n = 300, R = 200 and n = 130, R = 48 take 64-replica tiles; SK n = 2000 with
-    # 1024 replicas takes 128-replica tiles (8 MiB of state in the static array)
-    cases = [(inst.sk(300, 1), 200, 4), (inst.gnp_maxcut(130, 0.5, 2), 48, 9), (inst.sk(2000, 5), 1024, 11)]
+    # 1024 replicas takes 128-replica tiles (8 MiB of state in the static array);
+    # the last two store J in FP8 (widened in the kernel, no scratch for J)
+    cases = [(inst.sk(300, 1), 200, 4, "bf16"), (inst.gnp_maxcut(130, 0.5, 2), 48, 9, "bf16"),
+             (inst.sk(2000, 5), 1024, 11, "bf16"), (inst.sk(300, 6), 200, 4, "bf16_fp8j"),
+             (inst.sk(2000, 7), 1024, 12, "bf16_fp8j")]
     T = torch.as_tensor(inst.schedule(150), device=dev)
-    probs = [nmfa.Problem(J, precision="bf16") for J, _, _ in cases]
+    probs = [nmfa.Problem(J, precision=pr) for J, _, _, pr in cases]
     refs = []
-    for p, (J, R, seed) in zip(probs, cases):
+    for p, (J, R, seed, _) in zip(probs, cases):
         s, e, ei = _buffers(torch, R, p.n, dev)
         p.run_device(T, 0.15, 0.15, R, seed=seed, signs=s, energy=e, energy_i64=ei)
         p.sync()
@@ -45,7 +48,7 @@ def test_noalloc_matches_run_device_on_consecutive_calls():
     # two rounds of calls in a row, alternating sizes, so each call starts from the
     # scratch contents the previous one left behind
     for _ in range(2):
-        for p, (J, R, seed), ref in zip(probs, cases, refs):
+        for p, (J, R, seed, _), ref in zip(probs, cases, refs):
             s, e, ei = _buffers(torch, R, p.n, dev)
             nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, seed=seed, signs=s, energy=e, energy_i64=ei)
             p.sync()
