@@ -300,6 +300,33 @@ def test_forced_256_replica_tiles_match_128_replica_tiles(n, R, storage):
 
 
 @pytest.mark.parametrize("options", [0, 1])
+def test_variant_launches_side_by_side_or_in_turn(options):
+    # A batch with several tile variants runs one persistent launch per variant: side
+    # by side when all their CTAs fit the SMs together (first batch: a 64-, a 128- and
+    # an FP8 128-replica launch of a few tiles each), one after the other when they
+    # do not (second batch: 256-replica tiles on 128 CTAs beside 128-replica tiles
+    # on 64).  Every run equals its solo run either way, with and without a graph.
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    T = torch.as_tensor(inst.schedule(40), device=dev)
+    for defs in ([(inst.sk(300, 81), "bf16", 64), (inst.sk(1500, 82), "bf16", 256), (inst.sk(1500, 83), "bf16_fp8j", 256)],
+                 [(inst.sk(2048, 84), "bf16", 2048), (inst.sk(2048, 85), "bf16", 512)]):
+        problems = [nmfa.Problem(J, precision=pr) for J, pr, _ in defs]
+        specs = [(T, R, 60 + k, k) for k, (_, _, R) in enumerate(defs)]
+        alone = [_alone(p, *sp) for p, sp in zip(problems, specs)]
+        b, outs = _batch(problems, specs, options)
+        assert len(nmfa.nmfa_batch_plan(b)) == len(defs)
+        nmfa.nmfa_batch_launch(b)
+        nmfa.nmfa_batch_sync(b)
+        for (s, e), (sa, ea) in zip(outs, alone):
+            np.testing.assert_array_equal(s.cpu().numpy(), sa)
+            np.testing.assert_array_equal(e.cpu().numpy(), ea)
+        nmfa.nmfa_batch_destroy(b)
+        for p in problems:
+            p.close()
+
+
+@pytest.mark.parametrize("options", [0, 1])
 def test_set_stream_ids_reruns_with_fresh_noise(options):
     # A created batch is re-targeted at other noise streams (plan and workspace kept,
     # descriptors uploaded again): each execution equals the solo runs on the streams
