@@ -163,7 +163,10 @@ int nmfa_run_device(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
  *   signs_dev  R*n int8, required (no scratch is made for signs)
  *   energy_dev, energy_i64_dev  as in nmfa_run_device (may be NULL)
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
+ * device current); make that first call before any stream capture.  Called on a
+ * capturing stream, the run (plan upload, flag reset, kernel, energy kernel) is
+ * recorded into the caller's graph and neither waits for nor marks the handle's
+ * completion event: the graph orders it, and nmfa_sync does not track its replays.  Every call
  * uses the same array, so calls whose kernels overlap on the GPU (different
  * streams, different handles) race and give wrong results: serialise them.
  * Returns NMFA_EUNSUPPORTED for other precisions.

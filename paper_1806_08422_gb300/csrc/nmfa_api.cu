@@ -907,7 +907,13 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int rc;
   if ((rc = cuda_error(cudaSetDevice(p->device), "cudaSetDevice"))) return rc;
-  if ((rc = cuda_error(cudaStreamWaitEvent(st, p->done, 0), "stream wait"))) return rc;
+  // Inside a stream capture the call becomes part of the caller's graph, which orders
+  // it: the handle's completion event (recorded outside the capture) is neither waited
+  // for nor recorded then.
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if ((rc = cuda_error(cudaStreamIsCapturing(st, &capturing), "capture query"))) return rc;
+  const bool in_capture = capturing != cudaStreamCaptureStatusNone;
+  if (!in_capture && (rc = cuda_error(cudaStreamWaitEvent(st, p->done, 0), "stream wait"))) return rc;
   RunParams rp{};
   rp.T = T_dev;
   rp.t_f = t_f;
@@ -938,7 +944,7 @@ int nmfa_run_device_noalloc(nmfa_problem* p, const double* T_dev, int32_t t_f, d
     ep.integer_valued = p->integer_valued;
     if ((rc = launch_energy(ep, signs_dev, replicas, energy_dev, energy_i64_dev, st))) return rc;
   }
-  return cuda_error(cudaEventRecord(p->done, st), "event record");
+  return in_capture ? NMFA_OK : cuda_error(cudaEventRecord(p->done, st), "event record");
 }
 
 // ---------------------------------------------------------------------------

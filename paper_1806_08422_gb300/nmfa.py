@@ -157,7 +157,8 @@ def nmfa_run_device(handle, T_dev, sigma, alpha, replicas, seed=0, stream_id=0, 
 
 def nmfa_run_device_noalloc(handle, T_dev, sigma, alpha, replicas, seed=0, stream_id=0, signs=None, energy=None,
                             energy_i64=None, stream=None):
-    """nmfa_run_device for a BF16 problem without any allocation (static scratch)."""
+    """nmfa_run_device for a BF16 or FP8-stored problem without any allocation (static
+    scratch); capturable into a CUDA graph after a first call outside the capture."""
     _check(load().nmfa_run_device_noalloc(handle, _t_ptr(T_dev), int(T_dev.numel()), float(sigma), float(alpha),
                                           int(replicas), int(seed), int(stream_id), _t_ptr(signs), _t_ptr(energy),
                                           _t_ptr(energy_i64), _stream_ptr(stream)))

@@ -88,3 +88,38 @@ def test_noalloc_size_limit_at_the_boundary():
         torch.cuda.synchronize()
         assert int((s != 7).sum()) == 0  # nothing was launched
     p.close()
+
+
+def test_noalloc_inside_a_cuda_graph():
+    # The case the entry point exists for: the run is captured into a CUDA graph
+    # (after a first call outside the capture has looked up the static array), and
+    # each replay writes what nmfa_run_device returns for the same inputs.
+    import torch
+
+    from paper_1806_08422_gb300 import nmfa
+
+    dev = torch.device("cuda", 0)
+    J, R, seed = inst.sk(700, 9), 256, 3
+    p = nmfa.Problem(J, precision="bf16")
+    T = torch.as_tensor(inst.schedule(120), device=dev)
+    ref = _buffers(torch, R, p.n, dev)
+    p.run_device(T, 0.15, 0.15, R, seed=seed, signs=ref[0], energy=ref[1], energy_i64=ref[2])
+    p.sync()
+    got = _buffers(torch, R, p.n, dev)
+    nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, seed=seed, signs=got[0], energy=got[1], energy_i64=got[2])
+    p.sync()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            nmfa.nmfa_run_device_noalloc(p.handle, T, 0.15, 0.15, R, seed=seed, signs=got[0], energy=got[1],
+                                         energy_i64=got[2], stream=side)
+    for _ in range(2):
+        for b in got:
+            b.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[2], ref[2]) and torch.equal(got[1], ref[1])
+    del graph
+    p.close()
