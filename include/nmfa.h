@@ -226,7 +226,9 @@ typedef struct nmfa_batch nmfa_batch;
  * M = 256, each loading half of every state slice) wherever the problem allows it
  * (n rounded to 128 is a multiple of 256 and the pairs fit on the grid).  Not the
  * default: on GB300 the pairs run slower than one CTA per tile for the benchmark
- * workload.  Results do not change. */
+ * workload.  A pair sums its odd row block's couplings in the pair's K order, so
+ * results agree with one-CTA tiles to the BF16 path's rounding rather than bit for
+ * bit; pair runs are still independent of what else a batch holds. */
 #define NMFA_BATCH_PAIR128 32
 /* Test only: leave the first group's last row-block tile out of the plan.  Nothing
  * then publishes that tile's state, so the group's other tiles wait for a flag that

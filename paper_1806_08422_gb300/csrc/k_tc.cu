@@ -656,10 +656,15 @@ __device__ __forceinline__ bool epilogue_item(const TcGroup* __restrict__ g, int
 // both CTAs).  SUB is a template argument so that the control block's shared-memory
 // address stays a constant.
 //
-// K order: every tile of a group sweeps the group's K slices (row blocks) starting at
-// its pair-aligned row block (b & ~1) and wrapping; the two tiles of a CTA pair share
-// one MMA and therefore one order, and every tile variant uses the same rule, so the
-// FP32 sums of every output (and with them the results) do not depend on the variant.
+// K order: every one-CTA tile of a group sweeps the group's K slices (row blocks)
+// starting at its own row block b and wrapping, whatever its width (64, 128 or 256
+// replicas, BF16- or FP8-stored J), so the FP32 sums of every output, and with them the
+// results, do not depend on the width.  The two tiles of a CTA pair share one MMA and
+// therefore one order, starting at the pair's even row block (b & ~1): the pair's odd
+// tile sums in another order than a one-CTA tile would, so CTA-pair runs agree with
+// one-CTA runs to the BF16 path's rounding, not bit for bit.  (The shared order for
+// every variant cost 4-5 % on small and mid-size groups, whose odd row blocks then
+// waited for their partner's slice, which comes through L2, before their own.)
 template <int BN, int SUB, bool PAIR, bool F8>
 __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups, const TcItem* __restrict__ items,
                                              const int32_t* __restrict__ first, int32_t* status, SharedCtl* ctl_all,
@@ -736,7 +741,7 @@ __device__ __forceinline__ void run_pipeline(const TcGroup* __restrict__ groups,
       };
       const int brow = PAIR ? static_cast<int>(crank) * (bn / 2) : 0;  // this CTA's replica rows of S
       const int KB = n_pad / kKSlot;  // ring slots per step (= row blocks)
-      const int kslice_base = (b & ~1) % KB;
+      const int kslice_base = (PAIR ? (b & ~1) : b) % KB;
       if (lane == 0) {
         acquire_tensormap(tmJ);
         acquire_tensormap(tmS);
