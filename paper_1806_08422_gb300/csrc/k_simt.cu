@@ -17,6 +17,7 @@
 
 #include "nmfa_device.cuh"
 #include "nmfa_internal.h"
+#include "tc_ptx.cuh"
 
 namespace nmfa {
 
@@ -235,8 +236,9 @@ dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
   const int r0 = blockIdx.x * RC;
   const int R = rp.replicas;
   if constexpr (J_SMEM) {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Jsm[idx] = Jg[idx];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Jsm[idx] = Jg[(idx / n) * pb.ldj + idx % n];
   }
+  const int ldj = J_SMEM ? n : pb.ldj;
   const T* J = J_SMEM ? Jsm : Jg;
   init_state<T, RC>(S0, n, r0, R, rp.s0);
   __syncthreads();
@@ -256,7 +258,7 @@ dense_simt_kernel(DenseSimtProblem pb, RunParams rp) {
       const T* col = J + i;
 #pragma unroll 4
       for (int j = 0; j < n; ++j) {
-        const T jv = J_SMEM ? col[static_cast<int64_t>(j) * n] : __ldg(col + static_cast<int64_t>(j) * n);
+        const T jv = J_SMEM ? col[static_cast<int64_t>(j) * n] : __ldg(col + static_cast<int64_t>(j) * ldj);
         T sj[RC];
         lds_vec<T, RC>(cur + j * RC, sj);
 #pragma unroll
@@ -331,58 +333,144 @@ csr_kernel(CsrProblem pb, RunParams rp) {
 }
 
 // ----------------------------------------------------------------------------
-// FP32 dense path for large n: one launch per step of Algorithm 1.  Each CTA
-// computes a 128-spin x 64-replica tile of P = J S with a register-blocked CUDA-core
-// GEMM (8 x 4 outputs per thread, 16-deep K slices staged in shared memory; J is read
-// by rows because it is symmetric) and applies the rest of the step to its tile.
-// The state lives in two global FP32 buffers S[2][n][ld] (replicas contiguous).
+// FP32 dense path for large n: the whole run of Algorithm 1 in one cooperative
+// launch.  A step is the product P = J S of the couplings with the state (spins x
+// replicas) followed by the field, Boltzmann and mixing updates of every spin.
+//
+// Tiles.  P is cut into 128-spin x 64-replica tiles.  A CTA computes a tile with a
+// register-blocked CUDA-core GEMM (8 spins x 4 replicas per thread) over 32-deep K
+// slices of J and S that cp.async copies into a three-stage shared-memory ring, so
+// the copies of later slices overlap the arithmetic on the current one.  J is
+// symmetric, so row k of J holds column k and the A slice is read by rows.
+//
+// Split K.  When the tiles are fewer than half the co-resident CTAs, each tile's K
+// range is cut into `splits` ranges, one CTA each.  A range leaves its partial tile
+// in global scratch and counts itself in on the tile's counter; once all ranges of
+// the tile are in, each of its CTAs sums its share of the tile over the ranges in
+// range order (so a run is deterministic for a given split) and applies the update
+// to that share.  Without a split a CTA applies the update to its tile from
+// registers and takes the next tile.
+//
+// Steps.  A grid barrier (a counter that every CTA adds to and waits on) closes the
+// initialisation and every step; the state is double-buffered, S[2][n_pad][ld], so a
+// step reads one buffer and writes the other.  J is stored n_pad x n_pad and the
+// state n_pad x ld (n_pad = n rounded up to 128, ld = replicas rounded up to 64),
+// with zeros beyond n and beyond the replicas, so tiles need no bounds checks.
+// Every wait is bounded; on expiry the CTA records the timeout status and the
+// kernel returns (the other CTAs see the status while they wait and return too).
 // ----------------------------------------------------------------------------
-constexpr int kTBM = 128, kTBN = 64, kTBK = 16;
+constexpr int kFBM = 128, kFBN = 64, kFBK = 32, kFStages = 3, kFThreads = 256;
+constexpr int kFStageFloats = kFBK * (kFBM + kFBN);
+constexpr int kFSmemBytes = kFStages * kFStageFloats * static_cast<int>(sizeof(float));
+constexpr int kFTileFloats = kFBM * kFBN;
+constexpr uint64_t kF32WaitNs = 2000000000ull;
+constexpr uint64_t kF32StartWaitNs = 20000000000ull;
 
-struct TiledF32Step {
-  int n, R, ld, t;
-  const float* J;
+struct CoopF32 {
+  int n, n_pad, R, ld, t_f;
+  int tiles_m, tiles;        // row tiles; all tiles (row tiles x replica tiles)
+  int splits, sps;           // K ranges per tile and 32-deep slices per range
+  const float* J;            // n_pad x n_pad
   const float* h32;
   const float* inv_d32;
-  const float* S_cur;
-  float* S_next;
   const double* T;
   float sigma_ns, alpha, one_m_alpha;
   NoiseKey key;
   uint32_t stream;
+  const double* s0;          // R x n or nullptr
+  float* S;                  // 2 x n_pad x ld
+  float* part;               // tiles x splits x kFTileFloats (splits > 1)
+  uint32_t* tile_cnt;        // tiles (zero at launch)
+  uint32_t* bar;             // grid barrier counter (zero at launch)
+  int8_t* signs;
+  double* s_out;
   double* phi_out;
+  int32_t* status;
 };
 
-__global__ void __launch_bounds__(256) dense_tiled_f32_step_kernel(TiledF32Step a) {
-  __shared__ __align__(16) float As[kTBK][kTBM];
-  __shared__ __align__(16) float Bs[kTBK][kTBN];
-  __shared__ float s_inv_T;
-  const int n = a.n;
-  const int i0 = blockIdx.x * kTBM, r0 = blockIdx.y * kTBN;
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Thread 0 adds `add` to *cnt (release, after the CTA's writes) and waits until it
+// reaches `need` (acquire); the CTA then proceeds together.  False on timeout or
+// when another CTA has recorded a failure.
+__device__ __noinline__ bool coop_arrive_wait(uint32_t* cnt, uint32_t add, uint32_t need, int32_t* status,
+                                              uint64_t limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    ptx::red_release_gpu_add(cnt, add);
+    int good = 1;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    while (ptx::ld_acquire_gpu(cnt) < need) {
+      if (*reinterpret_cast<volatile int32_t*>(status) != kStatusOk) {
+        good = 0;
+        break;
+      }
+      if (ptx::globaltimer_ns() - t0 > limit_ns) {
+        atomicExch(status, static_cast<int32_t>(kStatusTimeout));
+        good = 0;
+        break;
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Copies K slice `slice` of the tile (rows i0.., replicas r0..) into ring stage `st`:
+// A[kk][ii] = J[k0 + kk][i0 + ii] (128 floats a row), B[kk][rr] = S[k0 + kk][r0 + rr].
+__device__ __forceinline__ void coop_load_slice(const CoopF32& a, const float* cur, float* ring, int st,
+                                                int slice, int i0, int r0) {
+  float* As = ring + st * kFStageFloats;
+  float* Bs = As + kFBK * kFBM;
+  const int k0 = slice * kFBK;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {  // 32 rows x 32 float4
+    const int e = threadIdx.x + kFThreads * u, kk = e >> 5, c4 = e & 31;
+    cp_async16(ptx::smem_u32(As + kk * kFBM + c4 * 4), a.J + static_cast<int64_t>(k0 + kk) * a.n_pad + i0 + c4 * 4);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {  // 32 rows x 16 float4
+    const int e = threadIdx.x + kFThreads * u, kk = e >> 4, c4 = e & 15;
+    cp_async16(ptx::smem_u32(Bs + kk * kFBN + c4 * 4), cur + static_cast<int64_t>(k0 + kk) * a.ld + r0 + c4 * 4);
+  }
+}
+
+// acc := the tile's product over K slices [s0, s1).  Returns with the ring free.
+__device__ __forceinline__ void coop_gemm(const CoopF32& a, const float* cur, float* ring, int i0, int r0, int s0,
+                                          int s1, float (&acc)[8][4]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  if (threadIdx.x == 0) s_inv_T = static_cast<float>(1.0 / a.T[a.t]);
-  float acc[8][4];
 #pragma unroll
   for (int m = 0; m < 8; ++m)
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
-  for (int k0 = 0; k0 < n; k0 += kTBK) {
+  const int ns = s1 - s0;
 #pragma unroll
-    for (int e = threadIdx.x; e < kTBK * kTBM; e += 256) {
-      const int kk = e / kTBM, ii = e % kTBM, k = k0 + kk, i = i0 + ii;
-      As[kk][ii] = (k < n && i < n) ? __ldg(a.J + static_cast<int64_t>(k) * n + i) : 0.0f;
-    }
+  for (int p = 0; p < kFStages - 1; ++p) {
+    if (p < ns) coop_load_slice(a, cur, ring, p, s0 + p, i0, r0);
+    cp_async_commit();
+  }
+  for (int s = 0; s < ns; ++s) {
+    cp_async_wait<kFStages - 2>();  // this thread's copies of slice s have landed
+    __syncthreads();                // everyone's have, and slice s - 1 is no longer read
+    if (s + kFStages - 1 < ns) coop_load_slice(a, cur, ring, (s + kFStages - 1) % kFStages, s0 + s + kFStages - 1, i0, r0);
+    cp_async_commit();
+    const float* As = ring + (s % kFStages) * kFStageFloats;
+    const float* Bs = As + kFBK * kFBM;
 #pragma unroll
-    for (int e = threadIdx.x; e < kTBK * kTBN; e += 256) {
-      const int kk = e / kTBN, rr = e % kTBN, k = k0 + kk, r = r0 + rr;
-      Bs[kk][rr] = (k < n && r < a.ld) ? a.S_cur[static_cast<int64_t>(k) * a.ld + r] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTBK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+    for (int kk = 0; kk < kFBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(As + kk * kFBM + ty * 8);
+      const float4 a1 = *reinterpret_cast<const float4*>(As + kk * kFBM + ty * 8 + 4);
+      const float4 bv = *reinterpret_cast<const float4*>(Bs + kk * kFBN + tx * 4);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
@@ -390,56 +478,114 @@ __global__ void __launch_bounds__(256) dense_tiled_f32_step_kernel(TiledF32Step 
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[m][k] = fmaf(av[m], bb[k], acc[m][k]);
     }
-    __syncthreads();
   }
-  const float inv_T = s_inv_T;
-  const int r = r0 + tx * 4;
-  if (r >= a.ld) return;
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// Algorithm 1's update of spin i for replicas r..r+3 (r < R, r a multiple of 4) from
+// the coupling sums P[0..3]: Phi = (h_i + P) / d_i + sigma z, s' = alpha (-tanh(Phi /
+// T)) + (1 - alpha) s; replicas at or beyond R stay zero.
+__device__ __forceinline__ void coop_update(const CoopF32& a, const float* cur, float* nxt, int t, float inv_T,
+                                            int i, int r, const float P[4], bool last) {
+  const float4 z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r >> 2), static_cast<uint32_t>(t),
+                                          static_cast<uint32_t>(i)));
+  const int64_t off = static_cast<int64_t>(i) * a.ld + r;
+  const float4 so = __ldcg(reinterpret_cast<const float4*>(cur + off));
+  const float zz[4] = {z.x, z.y, z.z, z.w};
+  const float sv[4] = {so.x, so.y, so.z, so.w};
+  const float hi = a.h32[i], inv_di = a.inv_d32[i];
+  float out[4], phi[4];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int i = i0 + ty * 8 + m;
-    if (i >= n) continue;
-    const float4 z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r >> 2), static_cast<uint32_t>(a.t),
-                                            static_cast<uint32_t>(i)));
-    const float4 so = *reinterpret_cast<const float4*>(a.S_cur + static_cast<int64_t>(i) * a.ld + r);
-    const float zz[4] = {z.x, z.y, z.z, z.w};
-    const float sv[4] = {so.x, so.y, so.z, so.w};
-    const float hi = a.h32[i], inv_di = a.inv_d32[i];
-    float out[4], phi[4];
+  for (int k = 0; k < 4; ++k) {
+    phi[k] = fmaf(a.sigma_ns, zz[k], (hi + P[k]) * inv_di);
+    out[k] = r + k < a.R ? fmaf(a.alpha, -tanhf(phi[k] * inv_T), a.one_m_alpha * sv[k]) : 0.0f;
+  }
+  __stcg(reinterpret_cast<float4*>(nxt + off), make_float4(out[0], out[1], out[2], out[3]));
+  if (last && a.phi_out != nullptr) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float P = hi + acc[m][k];
-      phi[k] = fmaf(a.sigma_ns, zz[k], P * inv_di);
-      out[k] = fmaf(a.alpha, -tanhf(phi[k] * inv_T), a.one_m_alpha * sv[k]);
-    }
-    *reinterpret_cast<float4*>(a.S_next + static_cast<int64_t>(i) * a.ld + r) = make_float4(out[0], out[1], out[2], out[3]);
-    if (a.phi_out != nullptr) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (r + k < a.R) a.phi_out[static_cast<int64_t>(r + k) * n + i] = static_cast<double>(phi[k]);
-    }
+    for (int k = 0; k < 4; ++k)
+      if (r + k < a.R) a.phi_out[static_cast<int64_t>(r + k) * a.n + i] = static_cast<double>(phi[k]);
   }
 }
 
-// S[0] := s0 (or 0) in the [n][ld] layout; replicas beyond R are zero.
-__global__ void tiled_f32_init_kernel(int n, int R, int ld, const double* s0, float* S) {
-  const int64_t total = static_cast<int64_t>(n) * ld;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(e / ld), r = static_cast<int>(e % ld);
-    S[e] = (s0 != nullptr && r < R) ? static_cast<float>(s0[static_cast<int64_t>(r) * n + i]) : 0.0f;
+__global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a) {
+  extern __shared__ __align__(16) float ring[];
+  const int n = a.n;
+  const int64_t plane = static_cast<int64_t>(a.n_pad) * a.ld;
+  // state 0 := s0 (or 0) on [n][R], zero elsewhere; state 1 := 0
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(kFThreads) + threadIdx.x; e < plane;
+       e += static_cast<int64_t>(gridDim.x) * kFThreads) {
+    const int i = static_cast<int>(e / a.ld), r = static_cast<int>(e % a.ld);
+    a.S[e] = (a.s0 != nullptr && i < n && r < a.R) ? static_cast<float>(a.s0[static_cast<int64_t>(r) * n + i]) : 0.0f;
+    a.S[plane + e] = 0.0f;
   }
-}
-
-// Sign readout (Algorithm 1) of the [n][ld] state into replica-major signs.
-__global__ void tiled_f32_readout_kernel(int n, int R, int ld, const float* S, int8_t* signs, double* s_out) {
-  const int64_t total = static_cast<int64_t>(n) * R;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  uint32_t phase = 1;
+  if (!coop_arrive_wait(a.bar, 1u, phase * gridDim.x, a.status, kF32StartWaitNs)) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int slices = a.n_pad / kFBK;
+  for (int t = 0; t < a.t_f; ++t) {
+    const float* cur = a.S + (t & 1) * plane;
+    float* nxt = a.S + ((t & 1) ^ 1) * plane;
+    const float inv_T = static_cast<float>(1.0 / a.T[t]);
+    const bool last = t == a.t_f - 1;
+    float acc[8][4];
+    if (a.splits == 1) {
+      for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+        const int i0 = (tile % a.tiles_m) * kFBM, r0 = (tile / a.tiles_m) * kFBN;
+        coop_gemm(a, cur, ring, i0, r0, 0, slices, acc);
+        const int r = r0 + tx * 4;
+        if (r < a.R) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const int i = i0 + ty * 8 + m;
+            if (i < n) coop_update(a, cur, nxt, t, inv_T, i, r, acc[m], last);
+          }
+        }
+      }
+    } else if (blockIdx.x < a.tiles * a.splits) {
+      const int tile = blockIdx.x / a.splits, q = blockIdx.x % a.splits;
+      const int i0 = (tile % a.tiles_m) * kFBM, r0 = (tile / a.tiles_m) * kFBN;
+      const int s0 = q * a.sps, s1 = min(slices, s0 + a.sps);
+      coop_gemm(a, cur, ring, i0, r0, s0, s1, acc);
+      float* mine = a.part + (static_cast<int64_t>(tile) * a.splits + q) * kFTileFloats;
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        __stcg(reinterpret_cast<float4*>(mine + (ty * 8 + m) * kFBN + tx * 4),
+               make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]));
+      if (!coop_arrive_wait(a.tile_cnt + tile, 1u, static_cast<uint32_t>(t + 1) * a.splits, a.status, kF32WaitNs))
+        return;
+      // this CTA's share of the tile: float4 columns [lo, hi) of the 128 x 16 grid
+      const int per = (kFTileFloats / 4 + a.splits - 1) / a.splits;
+      const int lo = q * per, hi = min(kFTileFloats / 4, lo + per);
+      const float* base = a.part + static_cast<int64_t>(tile) * a.splits * kFTileFloats;
+      for (int e = lo + threadIdx.x; e < hi; e += kFThreads) {
+        const int row = e >> 4, c4 = e & 15;
+        const int i = i0 + row, r = r0 + c4 * 4;
+        if (i >= n || r >= a.R) continue;
+        float P[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int qq = 0; qq < a.splits; ++qq) {
+          const float4 v = __ldcg(reinterpret_cast<const float4*>(base + qq * kFTileFloats + row * kFBN + c4 * 4));
+          P[0] += v.x;
+          P[1] += v.y;
+          P[2] += v.z;
+          P[3] += v.w;
+        }
+        coop_update(a, cur, nxt, t, inv_T, i, r, P, last);
+      }
+    }
+    ++phase;
+    if (!coop_arrive_wait(a.bar, 1u, phase * gridDim.x, a.status, kF32WaitNs)) return;
+  }
+  // sign readout (Algorithm 1) of the final state into replica-major signs
+  const float* fin = a.S + (a.t_f & 1) * plane;
+  const int64_t total = static_cast<int64_t>(n) * a.R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(kFThreads) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * kFThreads) {
     const int r = static_cast<int>(e / n), i = static_cast<int>(e % n);
-    const float s = S[static_cast<int64_t>(i) * ld + r];
-    signs[e] = s >= 0.0f ? int8_t(1) : int8_t(-1);
-    if (s_out != nullptr) s_out[e] = static_cast<double>(s);
+    const float s = __ldcg(fin + static_cast<int64_t>(i) * a.ld + r);
+    a.signs[e] = s >= 0.0f ? int8_t(1) : int8_t(-1);
+    if (a.s_out != nullptr) a.s_out[e] = static_cast<double>(s);
   }
 }
 
@@ -538,6 +684,108 @@ int pick_rc_csr(int n, int replicas, size_t elem, int requested) {
   return rc;
 }
 
+// Co-resident CTAs of the cooperative FP32 kernel on the current device.
+int coop_f32_capacity() {
+  static int cap = -1;
+  if (cap < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(dense_f32_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemBytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_f32_coop_kernel, kFThreads, kFSmemBytes);
+    cap = std::max(1, sms * per);
+  }
+  return cap;
+}
+
+// Tiles, K split and scratch layout of one run: [state 2 x n_pad x ld floats]
+// [partial tiles, when split][tile counters, grid barrier counter].
+struct CoopF32Plan {
+  int n_pad, ld, tiles_m, tiles, splits, sps, grid;
+  int64_t state_floats, part_floats, cnt_words;
+  int64_t bytes() const { return 4 * (state_floats + part_floats + cnt_words); }
+};
+
+CoopF32Plan plan_coop_f32(int n, int R) {
+  CoopF32Plan pl{};
+  pl.n_pad = (n + kFBM - 1) / kFBM * kFBM;
+  pl.ld = (R + kFBN - 1) / kFBN * kFBN;
+  pl.tiles_m = pl.n_pad / kFBM;
+  pl.tiles = pl.tiles_m * (pl.ld / kFBN);
+  const int slices = pl.n_pad / kFBK;
+  const int cap = coop_f32_capacity();
+  // Split K only while the tiles fill at most half of the co-resident CTAs; ranges
+  // of equal length (the last one shorter), none empty.
+  pl.splits = 2 * pl.tiles <= cap ? std::min(slices, cap / pl.tiles) : 1;
+  pl.sps = (slices + pl.splits - 1) / pl.splits;
+  pl.splits = (slices + pl.sps - 1) / pl.sps;
+  pl.grid = pl.splits > 1 ? pl.tiles * pl.splits : std::min(pl.tiles, cap);
+  pl.state_floats = 2ll * pl.n_pad * pl.ld;
+  pl.part_floats = pl.splits > 1 ? static_cast<int64_t>(pl.tiles) * pl.splits * kFTileFloats : 0;
+  pl.cnt_words = (pl.tiles + 1 + 63) / 64 * 64;
+  return pl;
+}
+
+}  // namespace
+
+int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas) { return plan_coop_f32(n, replicas).bytes(); }
+
+int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void* ws, int32_t* status,
+                           cudaStream_t st) {
+  const int n = pb.n, R = rp.replicas;
+  const CoopF32Plan pl = plan_coop_f32(n, R);
+  if (pb.ldj != pl.n_pad) return set_error(NMFA_EINVAL, "tiled FP32 path: J is not stored n_pad x n_pad");
+  // the barrier counter reaches (t_f + 1) x grid and the tile counters t_f x splits
+  if ((static_cast<int64_t>(rp.t_f) + 1) * pl.grid >= (int64_t(1) << 32))
+    return set_error(NMFA_EUNSUPPORTED, "tiled FP32 path: t_f too large for the step counters");
+  CoopF32 a{};
+  a.n = n;
+  a.n_pad = pl.n_pad;
+  a.R = R;
+  a.ld = pl.ld;
+  a.t_f = rp.t_f;
+  a.tiles_m = pl.tiles_m;
+  a.tiles = pl.tiles;
+  a.splits = pl.splits;
+  a.sps = pl.sps;
+  a.J = static_cast<const float*>(pb.J);
+  a.h32 = static_cast<const float*>(pb.h);
+  a.inv_d32 = pb.inv_d32;
+  a.T = rp.T;
+  a.sigma_ns = static_cast<float>(rp.sigma * rp.noise_sign);
+  a.alpha = static_cast<float>(rp.alpha);
+  a.one_m_alpha = static_cast<float>(1.0 - rp.alpha);
+  a.key = make_noise_key(rp.seed);
+  a.stream = rp.stream_id;
+  a.s0 = rp.s0;
+  a.S = static_cast<float*>(ws);
+  a.part = a.S + pl.state_floats;
+  a.tile_cnt = reinterpret_cast<uint32_t*>(a.part + pl.part_floats);
+  a.bar = a.tile_cnt + pl.tiles;
+  a.signs = rp.signs;
+  a.s_out = rp.s_out;
+  a.phi_out = rp.phi_out;
+  a.status = status;
+  int rc = cuda_error(cudaMemsetAsync(a.tile_cnt, 0, 4 * pl.cnt_words, st), "tiled FP32 counters");
+  if (rc) return rc;
+  // cooperative: every CTA is resident at once (the CTAs wait on one another at
+  // the grid barrier and the split tiles' counters)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(pl.grid);
+  cfg.blockDim = dim3(kFThreads);
+  cfg.dynamicSmemBytes = kFSmemBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t ce = cudaLaunchKernelEx(&cfg, dense_f32_coop_kernel, a);
+  count_launch();
+  return cuda_error(ce, "tiled FP32 kernel launch");
+}
+
+namespace {
 }  // namespace
 
 int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
@@ -557,50 +805,6 @@ int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp
     case 4: return launch_dense_rc<float, 4>(pb, rp, st);
     default: return launch_dense_rc<float, 8>(pb, rp, st);
   }
-}
-
-int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas) {
-  const int64_t ld = (replicas + 3) / 4 * 4;
-  return 2 * static_cast<int64_t>(n) * ld * 4;
-}
-
-int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, float* ws, cudaStream_t st) {
-  const int n = pb.n, R = rp.replicas;
-  const int ld = (R + 3) / 4 * 4;
-  float* S0 = ws;
-  float* S1 = ws + static_cast<int64_t>(n) * ld;
-  const int64_t total = static_cast<int64_t>(n) * ld;
-  const int gi = static_cast<int>(std::min<int64_t>((total + 255) / 256, 8192));
-  tiled_f32_init_kernel<<<std::max(gi, 1), 256, 0, st>>>(n, R, ld, rp.s0, S0);
-  count_launch();
-  TiledF32Step a{};
-  a.n = n;
-  a.R = R;
-  a.ld = ld;
-  a.J = static_cast<const float*>(pb.J);
-  a.h32 = static_cast<const float*>(pb.h);
-  a.inv_d32 = pb.inv_d32;
-  a.T = rp.T;
-  a.sigma_ns = static_cast<float>(rp.sigma * rp.noise_sign);
-  a.alpha = static_cast<float>(rp.alpha);
-  a.one_m_alpha = static_cast<float>(1.0 - rp.alpha);
-  a.key = make_noise_key(rp.seed);
-  a.stream = rp.stream_id;
-  const dim3 grid((n + kTBM - 1) / kTBM, (ld + kTBN - 1) / kTBN);
-  for (int t = 0; t < rp.t_f; ++t) {
-    a.t = t;
-    a.S_cur = (t & 1) ? S1 : S0;
-    a.S_next = (t & 1) ? S0 : S1;
-    a.phi_out = (t == rp.t_f - 1) ? rp.phi_out : nullptr;
-    dense_tiled_f32_step_kernel<<<grid, 256, 0, st>>>(a);
-  }
-  count_launch(static_cast<uint64_t>(rp.t_f));
-  const float* Sfin = (rp.t_f & 1) ? S1 : S0;
-  const int64_t tot2 = static_cast<int64_t>(n) * R;
-  const int go = static_cast<int>(std::min<int64_t>((tot2 + 255) / 256, 8192));
-  tiled_f32_readout_kernel<<<std::max(go, 1), 256, 0, st>>>(n, R, ld, Sfin, rp.signs, rp.s_out);
-  count_launch();
-  return cuda_error(cudaGetLastError(), "tiled FP32 kernels");
 }
 
 int launch_csr(bool fp64, const CsrProblem& pb, const RunParams& rp, cudaStream_t st,

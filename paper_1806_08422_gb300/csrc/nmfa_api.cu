@@ -539,8 +539,9 @@ int nmfa_create(int32_t n, const double* h, const double* J, int32_t precision, 
   if ((rc = finish_create(p, h))) return fail(rc);
   st = p->own_stream;
   if (precision == NMFA_FP32) {
-    if ((rc = dev_alloc_t(p, &p->J32, static_cast<size_t>(n) * n))) return fail(rc);
-    if ((rc = launch_convert_dense(n, p->J64, p->J32, 0, n, n, st))) return fail(rc);
+    // n_pad x n_pad with zeros beyond n: the tiled kernel's tiles need no bounds checks
+    if ((rc = dev_alloc_t(p, &p->J32, static_cast<size_t>(p->n_pad) * p->n_pad))) return fail(rc);
+    if ((rc = launch_convert_dense(n, p->J64, p->J32, 0, p->n_pad, p->n_pad, st))) return fail(rc);
   } else if (precision == NMFA_BF16 || precision == NMFA_BF16_FP8J) {
     const size_t elem = precision == NMFA_BF16 ? 2 : 1;
     void* q = nullptr;
@@ -765,13 +766,14 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
         DenseSimtProblem pb{};
         pb.n = p->n;
         pb.J = f64 ? static_cast<const void*>(p->J64) : static_cast<const void*>(p->J32);
+        pb.ldj = f64 ? p->n : p->n_pad;
         pb.h = f64 ? static_cast<const void*>(p->h64) : static_cast<const void*>(p->h32);
         pb.d = p->d64;
         pb.inv_d32 = p->inv_d32;
         if (!f64 && p->n >= kTiledF32MinN && p->replicas_per_cta == 0) {
           if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas)), p->done)))
             return rc;
-          rc = launch_dense_tiled_f32(pb, rp, static_cast<float*>(p->ws.p), st);
+          rc = launch_dense_tiled_f32(pb, rp, p->ws.p, p->status, st);
         } else {
           rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
         }

@@ -55,18 +55,23 @@ struct RunParams {
 // ---- CUDA-core dense path (FP32 / FP64) -----------------------------------
 struct DenseSimtProblem {
   int32_t n;
-  const void* J;          // float or double, row-major n*n (symmetric)
+  int32_t ldj;            // row stride of J in elements (n for FP64; n rounded up to 128 for FP32)
+  const void* J;          // float or double, row-major, symmetric; FP32 J is n_pad x n_pad, zero-padded
   const void* h;          // float or double, n (zeros when h = 0)
   const double* d;        // FP64 row norms
   const float* inv_d32;   // 1/d_i in binary32 (0 where d_i = 0)
 };
 int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp,
                       cudaStream_t st, int replicas_per_cta);
-// FP32 dense path for large n: per-step register-blocked GEMM + fused update, state
-// in a caller-provided scratch of tiled_f32_workspace_bytes(n, R) bytes.
+// FP32 dense path for large n: the whole run in one cooperative launch (register-
+// blocked GEMM tiles, split along K when the tiles are fewer than the CTAs, fused
+// update, a grid barrier per step).  State, partial tiles and counters live in a
+// caller-provided scratch of tiled_f32_workspace_bytes(n, R) bytes; bounded waits
+// report through `status`.
 int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas);
-int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, float* ws, cudaStream_t st);
-// n from which the FP32 dense path switches to the tiled per-step kernel.
+int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void* ws, int32_t* status,
+                           cudaStream_t st);
+// n from which the FP32 dense path switches to the tiled kernel.
 constexpr int32_t kTiledF32MinN = 512;
 
 // ---- CUDA-core CSR path (FP32 / FP64) ---------------------------------------

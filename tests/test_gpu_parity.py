@@ -126,45 +126,72 @@ def test_second_step_reads_every_row_blocks_first_step_state(n, R):
     assert (np.abs(stale - ref) / scale).max() > 10 * TOL["bf16"]
 
 
-@pytest.mark.parametrize("n,R", [(384, 200), (1100, 256)])
-def test_bf16_five_steps_sigma0(n, R):
-    # Five steps of the tensor path from a random state, sigma = 0, alpha = 0.15 (the
-    # paper's), state after every step against the oracle's:
+# Five-step cases: the tensor path (64-replica tiles over 3 row blocks; 128-replica
+# tiles over 9 row blocks with a ragged tail) and the FP32 tiled kernel (n >= 512,
+# 128-spin x 64-replica tiles; its K split depends on the co-resident CTAs, here for
+# 152 SMs x 2): 18 tiles cut into 12 K ranges, 90 tiles into 3, 216 tiles one per CTA,
+# and 320 tiles, two for some CTAs.
+FIVE_STEP_CASES = [("bf16", 384, 200), ("bf16", 1100, 256), ("fp32", 700, 130), ("fp32", 1100, 600),
+                   ("fp32", 1500, 1100), ("fp32", 2500, 1000)]
+
+
+@pytest.mark.parametrize("prec,n,R", FIVE_STEP_CASES)
+def test_five_steps_sigma0(prec, n, R):
+    # Five steps from a random state, sigma = 0, alpha = 0.15 (the paper's), state
+    # after every step against the oracle's:
     #  (a) step k from the GPU's own state after k - 1 steps (runs are deterministic at
     #      sigma = 0, so a (k-1)-step run gives exactly that state): Phi within the
-    #      BF16 tolerance and the new state within that tolerance carried through tanh;
+    #      path's tolerance and the new state within that tolerance carried through tanh;
     #  (b) k steps from s0 against the oracle's k steps from s0, within the bound
     #      e_k = (1 - alpha) e_(k-1) + alpha (dPhi_k / T_k + rounding), where
     #      dPhi_k = tol scale_k + (|J| e_(k-1)) / d carries the earlier steps' error
     #      through the coupling sum.
+    # With sigma = 0 the replicas evolve independently, so for more than 256 replicas
+    # the oracle follows 24 of them (both ends and the middle of the replica range).
     J = inst.sk(n, 400 + n)
     s0 = _rand_state(R, n, 401)
+    idx = np.arange(R) if R <= 256 else np.r_[0:8, R // 2:R // 2 + 8, R - 8:R]
     # temperatures scaled with sqrt(n - 1) = sum_j |J_ij| / d_i, the factor by which a
     # state error can grow through one coupling sum, so the bound stays small
     c = np.sqrt((n - 1) / 383.0)
     T = [c * x for x in (8.0, 6.0, 5.0, 4.0, 3.0)]
     alpha = 0.15
-    g = Gpu(J, precision="bf16")
+    tol = TOL[prec]
+    g = Gpu(J, precision=prec)
     runs = [g.run(T[:k], 0.0, alpha, R, s0=s0, want_state=True, want_phi=True) for k in range(1, 6)]
     g.close()
     d = oracle.row_norms(J)
     absJ = np.abs(J)
+    s0 = s0[idx]
     prev_gpu = s0
     e = np.zeros_like(s0)
     for k in range(1, 6):
-        out = runs[k - 1]
+        out = {"phi": runs[k - 1]["phi"][idx], "state": runs[k - 1]["state"][idx]}
         Tk = T[k - 1]
-        one = oracle.run(J, [Tk], 0.0, alpha, R, s0=prev_gpu, want_phi=True, want_state=True)
+        one = oracle.run(J, [Tk], 0.0, alpha, len(idx), s0=prev_gpu, want_phi=True, want_state=True)
         scale = (np.abs(prev_gpu) @ absJ.T) / d[None, :]
-        assert (np.abs(out["phi"] - one["phi"]) / scale).max() <= TOL["bf16"], k
-        _check_update("bf16", alpha, Tk, prev_gpu, out, one, TOL["bf16"] * scale)
-        ref = oracle.run(J, T[:k], 0.0, alpha, R, s0=s0, want_phi=True, want_state=True)
-        dphi = TOL["bf16"] * scale + (e @ absJ.T) / d[None, :]
-        e = (1.0 - alpha) * e + update_tol("bf16", alpha, Tk, ref["phi"], dphi)
+        assert (np.abs(out["phi"] - one["phi"]) / scale).max() <= tol, k
+        _check_update(prec, alpha, Tk, prev_gpu, out, one, tol * scale)
+        ref = oracle.run(J, T[:k], 0.0, alpha, len(idx), s0=s0, want_phi=True, want_state=True)
+        dphi = tol * scale + (e @ absJ.T) / d[None, :]
+        e = (1.0 - alpha) * e + update_tol(prec, alpha, Tk, ref["phi"], dphi)
         assert np.all(np.abs(out["state"] - ref["state"]) <= e), (k, float(np.max(np.abs(out["state"] - ref["state"]) / e)))
         prev_gpu = out["state"]
     # the bound is tight enough to see a dropped memory term (1 - alpha) s
     assert np.max(e) < 0.1 * (1.0 - alpha) * np.mean(np.abs(s0))
+
+
+def test_fp32_tiled_zero_steps_keep_the_initial_state():
+    # t_f = 0 on the FP32 tiled kernel: the state is s0 in binary32 and the signs its
+    # signs (the initialisation and readout around the steps, with padded tiles)
+    n, R = 700, 130
+    J = inst.sk(n, 9)
+    s0 = _rand_state(R, n, 10)
+    g = Gpu(J, precision="fp32")
+    out = g.run([], 0.15, 0.15, R, s0=s0, want_state=True)
+    g.close()
+    np.testing.assert_array_equal(out["state"], s0.astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(out["signs"], np.where(s0 >= 0, 1, -1))
 
 
 @pytest.mark.parametrize("prec", DENSE)
