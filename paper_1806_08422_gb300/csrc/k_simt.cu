@@ -363,6 +363,7 @@ constexpr int kFBM = 128, kFBN = 64, kFBK = 32, kFStages = 3, kFThreads = 256;
 constexpr int kFStageFloats = kFBK * (kFBM + kFBN);
 constexpr int kFSmemBytes = kFStages * kFStageFloats * static_cast<int>(sizeof(float));
 constexpr int kFTileFloats = kFBM * kFBN;
+constexpr int kFShareMax = (kFTileFloats / 4 / 2 + kFThreads - 1) / kFThreads;  // cells a thread reduces (splits >= 2)
 constexpr uint64_t kF32WaitNs = 2000000000ull;
 constexpr uint64_t kF32StartWaitNs = 20000000000ull;
 
@@ -397,16 +398,19 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Thread 0 adds `add` to *cnt (release, after the CTA's writes) and waits until it
-// reaches `need` (acquire); the CTA then proceeds together.  False on timeout or
-// when another CTA has recorded a failure.
-__device__ __noinline__ bool coop_arrive_wait(uint32_t* cnt, uint32_t add, uint32_t need, int32_t* status,
-                                              uint64_t limit_ns) {
-  __shared__ int ok;
+// Counter barriers.  coop_arrive: once every thread of the CTA has made its writes,
+// thread 0 adds one to *cnt with release semantics (the CTA barrier before it orders
+// the other threads' writes first).  coop_wait: thread 0 polls *cnt with acquire loads
+// until it reaches `need`, then the CTA proceeds together.  False on timeout (the CTA
+// records the timeout status) or when another CTA has recorded a failure.  The CTA
+// may do independent work between the two.
+__device__ __forceinline__ void coop_arrive(uint32_t* cnt) {
   __syncthreads();
+  if (threadIdx.x == 0) ptx::red_release_gpu_add(cnt, 1u);
+}
+__device__ __noinline__ bool coop_wait(const uint32_t* cnt, uint32_t need, int32_t* status, uint64_t limit_ns) {
+  __shared__ int ok;
   if (threadIdx.x == 0) {
-    __threadfence();
-    ptx::red_release_gpu_add(cnt, add);
     int good = 1;
     const uint64_t t0 = ptx::globaltimer_ns();
     while (ptx::ld_acquire_gpu(cnt) < need) {
@@ -483,15 +487,20 @@ __device__ __forceinline__ void coop_gemm(const CoopF32& a, const float* cur, fl
   __syncthreads();
 }
 
+// Noise of spin i for replicas r..r+3 at step t, and their state before the step.
+__device__ __forceinline__ void coop_inputs(const CoopF32& a, const float* cur, int t, int i, int r, float4& z,
+                                            float4& so) {
+  z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r >> 2), static_cast<uint32_t>(t),
+                             static_cast<uint32_t>(i)));
+  so = __ldcg(reinterpret_cast<const float4*>(cur + static_cast<int64_t>(i) * a.ld + r));
+}
+
 // Algorithm 1's update of spin i for replicas r..r+3 (r < R, r a multiple of 4) from
-// the coupling sums P[0..3]: Phi = (h_i + P) / d_i + sigma z, s' = alpha (-tanh(Phi /
-// T)) + (1 - alpha) s; replicas at or beyond R stay zero.
-__device__ __forceinline__ void coop_update(const CoopF32& a, const float* cur, float* nxt, int t, float inv_T,
-                                            int i, int r, const float P[4], bool last) {
-  const float4 z = gauss4_f32(noise_words(a.key, a.stream, static_cast<uint32_t>(r >> 2), static_cast<uint32_t>(t),
-                                          static_cast<uint32_t>(i)));
-  const int64_t off = static_cast<int64_t>(i) * a.ld + r;
-  const float4 so = __ldcg(reinterpret_cast<const float4*>(cur + off));
+// the coupling sums P[0..3], the draws z and the old state so: Phi = (h_i + P) / d_i +
+// sigma z, s' = alpha (-tanh(Phi / T)) + (1 - alpha) s; replicas at or beyond R stay
+// zero.
+__device__ __forceinline__ void coop_apply(const CoopF32& a, float* nxt, float inv_T, int i, int r,
+                                           const float P[4], float4 z, float4 so, bool last) {
   const float zz[4] = {z.x, z.y, z.z, z.w};
   const float sv[4] = {so.x, so.y, so.z, so.w};
   const float hi = a.h32[i], inv_di = a.inv_d32[i];
@@ -501,7 +510,8 @@ __device__ __forceinline__ void coop_update(const CoopF32& a, const float* cur, 
     phi[k] = fmaf(a.sigma_ns, zz[k], (hi + P[k]) * inv_di);
     out[k] = r + k < a.R ? fmaf(a.alpha, -tanhf(phi[k] * inv_T), a.one_m_alpha * sv[k]) : 0.0f;
   }
-  __stcg(reinterpret_cast<float4*>(nxt + off), make_float4(out[0], out[1], out[2], out[3]));
+  __stcg(reinterpret_cast<float4*>(nxt + static_cast<int64_t>(i) * a.ld + r),
+         make_float4(out[0], out[1], out[2], out[3]));
   if (last && a.phi_out != nullptr) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -521,7 +531,8 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
     a.S[plane + e] = 0.0f;
   }
   uint32_t phase = 1;
-  if (!coop_arrive_wait(a.bar, 1u, phase * gridDim.x, a.status, kF32StartWaitNs)) return;
+  coop_arrive(a.bar);
+  if (!coop_wait(a.bar, phase * gridDim.x, a.status, kF32StartWaitNs)) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int slices = a.n_pad / kFBK;
   for (int t = 0; t < a.t_f; ++t) {
@@ -539,7 +550,11 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int i = i0 + ty * 8 + m;
-            if (i < n) coop_update(a, cur, nxt, t, inv_T, i, r, acc[m], last);
+            if (i < n) {
+              float4 z, so;
+              coop_inputs(a, cur, t, i, r, z, so);
+              coop_apply(a, nxt, inv_T, i, r, acc[m], z, so, last);
+            }
           }
         }
       }
@@ -553,16 +568,27 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
       for (int m = 0; m < 8; ++m)
         __stcg(reinterpret_cast<float4*>(mine + (ty * 8 + m) * kFBN + tx * 4),
                make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]));
-      if (!coop_arrive_wait(a.tile_cnt + tile, 1u, static_cast<uint32_t>(t + 1) * a.splits, a.status, kF32WaitNs))
-        return;
-      // this CTA's share of the tile: float4 columns [lo, hi) of the 128 x 16 grid
+      coop_arrive(a.tile_cnt + tile);
+      // this CTA's share of the tile, float4 cells [lo, hi) of its 128 x 16 grid (at
+      // most kFShareMax a thread, as splits >= 2): noise and old state are fetched
+      // while the other K ranges of the tile come in
       const int per = (kFTileFloats / 4 + a.splits - 1) / a.splits;
       const int lo = q * per, hi = min(kFTileFloats / 4, lo + per);
+      float4 zq[kFShareMax], sq[kFShareMax];
+#pragma unroll
+      for (int j = 0; j < kFShareMax; ++j) {
+        const int e = lo + threadIdx.x + kFThreads * j;
+        const int i = i0 + (e >> 4), r = r0 + (e & 15) * 4;
+        if (e < hi && i < n && r < a.R) coop_inputs(a, cur, t, i, r, zq[j], sq[j]);
+      }
+      if (!coop_wait(a.tile_cnt + tile, static_cast<uint32_t>(t + 1) * a.splits, a.status, kF32WaitNs)) return;
       const float* base = a.part + static_cast<int64_t>(tile) * a.splits * kFTileFloats;
-      for (int e = lo + threadIdx.x; e < hi; e += kFThreads) {
+#pragma unroll
+      for (int j = 0; j < kFShareMax; ++j) {
+        const int e = lo + threadIdx.x + kFThreads * j;
         const int row = e >> 4, c4 = e & 15;
         const int i = i0 + row, r = r0 + c4 * 4;
-        if (i >= n || r >= a.R) continue;
+        if (e >= hi || i >= n || r >= a.R) continue;
         float P[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int qq = 0; qq < a.splits; ++qq) {
           const float4 v = __ldcg(reinterpret_cast<const float4*>(base + qq * kFTileFloats + row * kFBN + c4 * 4));
@@ -571,11 +597,12 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
           P[2] += v.z;
           P[3] += v.w;
         }
-        coop_update(a, cur, nxt, t, inv_T, i, r, P, last);
+        coop_apply(a, nxt, inv_T, i, r, P, zq[j], sq[j], last);
       }
     }
     ++phase;
-    if (!coop_arrive_wait(a.bar, 1u, phase * gridDim.x, a.status, kF32WaitNs)) return;
+    coop_arrive(a.bar);
+    if (!coop_wait(a.bar, phase * gridDim.x, a.status, kF32WaitNs)) return;
   }
   // sign readout (Algorithm 1) of the final state into replica-major signs
   const float* fin = a.S + (a.t_f & 1) * plane;

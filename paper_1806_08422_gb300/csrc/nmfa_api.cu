@@ -770,7 +770,7 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
         pb.h = f64 ? static_cast<const void*>(p->h64) : static_cast<const void*>(p->h32);
         pb.d = p->d64;
         pb.inv_d32 = p->inv_d32;
-        if (!f64 && p->n >= kTiledF32MinN && p->replicas_per_cta == 0) {
+        if (!f64 && tiled_f32_preferred(p->n, replicas) && p->replicas_per_cta == 0) {
           if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas)), p->done)))
             return rc;
           rc = launch_dense_tiled_f32(pb, rp, p->ws.p, p->status, st);

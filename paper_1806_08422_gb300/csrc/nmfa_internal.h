@@ -71,8 +71,15 @@ int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp
 int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas);
 int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void* ws, int32_t* status,
                            cudaStream_t st);
-// n from which the FP32 dense path switches to the tiled kernel.
-constexpr int32_t kTiledF32MinN = 512;
+// Which FP32 dense problems take the tiled kernel: from n = 256 spins, and above
+// n = 128 when there are more than 512 replicas.  Below that the replica-resident
+// kernel (no grid barrier) is faster; above it that kernel's per-spin loop over n
+// couplings read from L2 sets the step time (measured on GB300, 1000-step runs, ms,
+// replica-resident against tiled for R = 64 / 256 / 1024: n = 128: 1.6 / 1.9 / 2.6
+// against 7.7 / 8.3 / 8.3; n = 192: 3.2 / 4.1 / 15.2 against 7.3 / 7.5 / 10.4;
+// n = 256: 19.9 / 20.8 / 21.6 against 7.5 / 7.4 / 10.5; n = 384: 60.6 / 61.1 / 63.3
+// against 7.7 / 7.8 / 15.2).
+inline bool tiled_f32_preferred(int32_t n, int32_t replicas) { return n >= 256 || (n > 128 && replicas > 512); }
 
 // ---- CUDA-core CSR path (FP32 / FP64) ---------------------------------------
 struct CsrProblem {

@@ -1,14 +1,15 @@
-"""Time the tensor kernel on single SK +-1 instances across sizes and storage of J.
+"""Time the annealing kernels on single SK +-1 instances across sizes and storage of J.
 
 For each (N, R) and each storage of the couplings (BF16, or FP8-E4M3 widened to BF16
-in the kernel) the driver runs R replicas of Algorithm 1 for t_f steps in one
-persistent launch on device buffers (energies formed in the kernel) and reports the
-launch time per step, the tile plan, the algorithmic rate 2 N^2 R per product against
-the burst BF16 peak of MEASURED_PEAKS.json, and the best energy.  Both storages of the
+in the kernel, on the tensor path; or FP32 on the CUDA-core path) the driver runs R
+replicas of Algorithm 1 for t_f steps in one persistent launch on device buffers and
+reports the launch time per step, the tile plan, the algorithmic rate 2 N^2 R per
+product against the burst BF16 peak of MEASURED_PEAKS.json (tensor path) or the
+measured FP32 FMA rate (FP32 path), and the best energy.  Both tensor storages of the
 same instance give bit-identical runs, so their energies must agree.
 
     python -m paper_1806_08422_gb300.sizes [--sizes 8192:512,2000:1024] [--t-f 200]
-                                           [--storage bf16,bf16_fp8j] [--reps 3] [--options 0]
+                                           [--storage bf16,bf16_fp8j,fp32] [--reps 3] [--options 0]
 
 Prints one JSON line.  This module only drives the C ABI.
 """
@@ -66,6 +67,35 @@ def time_one(J, R, t_f, storage, reps, options=0):
             "min_energy": int(e.min().item()), "device_bytes": info["device_bytes"]}
 
 
+def time_fp32(J, R, t_f, reps):
+    """The FP32 CUDA-core path (one cooperative launch per run); the launch time is
+    taken by the library's profile events around the annealing kernel."""
+    import torch
+    dev = torch.device("cuda", 0)
+    n = J.shape[0]
+    p = nmfa.Problem(J, precision="fp32")
+    T = torch.as_tensor(inst.schedule(t_f), device=dev)
+    s = torch.empty((R, n), dtype=torch.int8, device=dev)
+    e = torch.empty(R, dtype=torch.int64, device=dev)
+    st = torch.cuda.Stream()
+    nmfa.nmfa_profile_enable(p.handle, True)
+    try:
+        p.run_device(T, 0.15, 0.15, R, signs=s, energy_i64=e, stream=st)  # warm-up
+        p.sync()
+        ms = []
+        for _ in range(reps):
+            p.run_device(T, 0.15, 0.15, R, signs=s, energy_i64=e, stream=st)
+            p.sync()
+            ms.append(nmfa.nmfa_last_kernel_ms(p.handle))
+        info = p.info()
+    finally:
+        p.close()
+    med = statistics.median(ms)
+    return {"ms_per_launch": med, "us_per_step": 1e3 * med / t_f, "plan": "FP32 CUDA-core tiles",
+            "tflops": 2.0 * n * n * R * t_f / (med * 1e-3) / 1e12,
+            "min_energy": int(e.min().item()), "device_bytes": info["device_bytes"]}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--sizes", default="8192:512,2000:1024")
@@ -77,17 +107,26 @@ def main():
                     help="nmfa_batch_create options, e.g. 16 / 64 to force 128 / 256 replicas per tile")
     args = ap.parse_args()
     peak = burst_peak()
+    storages = args.storage.split(",")
+    fp32_peak = None
+    if "fp32" in storages:
+        fp32_peak = nmfa.nmfa_measure_alu_peaks()["fp32_fma_tflops"]
     out = []
     for item in args.sizes.split(","):
         n, R = (int(x) for x in item.split(":"))
         J = inst.sk(n, args.seed)
         row = {"n": n, "replicas": R}
-        for storage in args.storage.split(","):
-            r = time_one(J, R, args.t_f, storage, args.reps, args.options)
-            r["frac_of_burst_bf16"] = r["tflops"] / peak
+        for storage in storages:
+            if storage == "fp32":
+                r = time_fp32(J, R, args.t_f, args.reps)
+                r["frac_of_fp32_fma"] = r["tflops"] / fp32_peak
+            else:
+                r = time_one(J, R, args.t_f, storage, args.reps, args.options)
+                r["frac_of_burst_bf16"] = r["tflops"] / peak
             row[storage] = r
         out.append(row)
-    print(json.dumps({"t_f": args.t_f, "options": args.options, "burst_bf16_tflops": peak, "runs": out}))
+    print(json.dumps({"t_f": args.t_f, "options": args.options, "burst_bf16_tflops": peak,
+                      "fp32_fma_tflops": fp32_peak, "runs": out}))
 
 
 if __name__ == "__main__":

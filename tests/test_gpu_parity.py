@@ -26,7 +26,7 @@ def _rand_state(R, n, seed):
 
 # ---------------------------------------------------------------- single step
 @pytest.mark.parametrize("prec", DENSE)
-@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64), (700, 130)])
+@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64), (700, 130), (200, 1030)])
 def test_single_step_phi(prec, n, R):
     J = inst.sk(n, 100 + n) if n > 1 else np.zeros((1, 1))
     h = inst.random_fields(n, 0.5, 7) if prec != "bf16" else None
@@ -127,7 +127,7 @@ def test_second_step_reads_every_row_blocks_first_step_state(n, R):
 
 
 # Five-step cases: the tensor path (64-replica tiles over 3 row blocks; 128-replica
-# tiles over 9 row blocks with a ragged tail) and the FP32 tiled kernel (n >= 512,
+# tiles over 9 row blocks with a ragged tail) and the FP32 tiled kernel (n >= 256,
 # 128-spin x 64-replica tiles; its K split depends on the co-resident CTAs, here for
 # 152 SMs x 2): 18 tiles cut into 12 K ranges, 90 tiles into 3, 216 tiles one per CTA,
 # and 320 tiles, two for some CTAs.
