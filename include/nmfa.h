@@ -348,6 +348,15 @@ int nmfa_last_kernel_ms(nmfa_problem* p, float* ms);
  * 1, 2, 4 or 8).  Results do not depend on it. */
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t replicas_per_cta);
 
+/* nmfa_debug_withhold_arrival -- test entry (not part of the stable ABI), for
+ * testing failure detection without a GPU fault: on the FP32 tiled path (dense FP32
+ * problems of n >= 256, and n > 128 with more than 512 replicas) the first CTA of
+ * the following runs of `p` does not arrive at the grid barrier that closes step
+ * `step` (-1: off, the default).  The other CTAs' bounded waits then give up (after
+ * about 2 s), nmfa_sync reports NMFA_ETIMEOUT, and the next run is unaffected.
+ * Returns NMFA_EINVAL for a NULL handle or step < -1. */
+int nmfa_debug_withhold_arrival(nmfa_problem* p, int32_t step);
+
 /* Measured CUDA-core arithmetic peaks of the current device, the denominators of
  * the CUDA-core paths' rooflines: out[0] = FP32 FMA throughput, out[1] = FP64 FMA
  * throughput, both in TFLOP/s (2 flops per FMA), out[2] = tanh.approx.f32 throughput

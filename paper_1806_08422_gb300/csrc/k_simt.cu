@@ -387,6 +387,7 @@ struct CoopF32 {
   double* s_out;
   double* phi_out;
   int32_t* status;
+  int withhold_step;         // >= 0: CTA 0 does not arrive at the barrier closing this step
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -601,7 +602,10 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
       }
     }
     ++phase;
-    coop_arrive(a.bar);
+    if (blockIdx.x == 0 && t == a.withhold_step)
+      __syncthreads();
+    else
+      coop_arrive(a.bar);
     if (!coop_wait(a.bar, phase * gridDim.x, a.status, kF32WaitNs)) return;
   }
   // sign readout (Algorithm 1) of the final state into replica-major signs
@@ -758,7 +762,7 @@ CoopF32Plan plan_coop_f32(int n, int R) {
 int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas) { return plan_coop_f32(n, replicas).bytes(); }
 
 int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void* ws, int32_t* status,
-                           cudaStream_t st) {
+                           int32_t withhold_step, cudaStream_t st) {
   const int n = pb.n, R = rp.replicas;
   const CoopF32Plan pl = plan_coop_f32(n, R);
   if (pb.ldj != pl.n_pad) return set_error(NMFA_EINVAL, "tiled FP32 path: J is not stored n_pad x n_pad");
@@ -793,6 +797,7 @@ int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void
   a.s_out = rp.s_out;
   a.phi_out = rp.phi_out;
   a.status = status;
+  a.withhold_step = withhold_step;
   int rc = cuda_error(cudaMemsetAsync(a.tile_cnt, 0, 4 * pl.cnt_words, st), "tiled FP32 counters");
   if (rc) return rc;
   // cooperative: every CTA is resident at once (the CTAs wait on one another at

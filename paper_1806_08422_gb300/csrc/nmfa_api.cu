@@ -151,6 +151,7 @@ struct nmfa_problem {
   bool profiling = false;
   bool prof_valid = false;
   int replicas_per_cta = 0;  // CUDA-core paths: 0 = automatic
+  int32_t withhold_step = -1;  // nmfa_debug_withhold_arrival
   std::mutex mu;
 };
 
@@ -773,7 +774,7 @@ static int run_impl(nmfa_problem* p, const double* T_dev, int32_t t_f, double si
         if (!f64 && tiled_f32_preferred(p->n, replicas) && p->replicas_per_cta == 0) {
           if ((rc = ensure_buf(p->ws, static_cast<size_t>(tiled_f32_workspace_bytes(p->n, replicas)), p->done)))
             return rc;
-          rc = launch_dense_tiled_f32(pb, rp, p->ws.p, p->status, st);
+          rc = launch_dense_tiled_f32(pb, rp, p->ws.p, p->status, p->withhold_step, st);
         } else {
           rc = launch_dense_simt(f64, pb, rp, st, p->replicas_per_cta);
         }
@@ -1263,6 +1264,13 @@ int nmfa_batch_plan(const nmfa_batch* b, int32_t* bn, int32_t* ctas_per_mma, int
 }
 
 // Tuning hook for the CUDA-core paths (replicas per CTA: 0 = automatic, else 1/2/4/8).
+int nmfa_debug_withhold_arrival(nmfa_problem* p, int32_t step) {
+  if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
+  if (step < -1) return set_error(NMFA_EINVAL, "step must be >= -1");
+  p->withhold_step = step;
+  return NMFA_OK;
+}
+
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t rc) {
   if (p == nullptr) return set_error(NMFA_EINVAL, "NULL handle");
   if (rc != 0 && rc != 1 && rc != 2 && rc != 4 && rc != 8) return set_error(NMFA_EINVAL, "rc must be 0, 1, 2, 4 or 8");

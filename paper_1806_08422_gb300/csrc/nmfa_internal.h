@@ -67,10 +67,11 @@ int launch_dense_simt(bool fp64, const DenseSimtProblem& pb, const RunParams& rp
 // blocked GEMM tiles, split along K when the tiles are fewer than the CTAs, fused
 // update, a grid barrier per step).  State, partial tiles and counters live in a
 // caller-provided scratch of tiled_f32_workspace_bytes(n, R) bytes; bounded waits
-// report through `status`.
+// report through `status`.  withhold_step >= 0: the first CTA does not arrive at the
+// grid barrier closing that step (a test of the bounded waits).
 int64_t tiled_f32_workspace_bytes(int32_t n, int32_t replicas);
 int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void* ws, int32_t* status,
-                           cudaStream_t st);
+                           int32_t withhold_step, cudaStream_t st);
 // Which FP32 dense problems take the tiled kernel: from n = 256 spins, and above
 // n = 128 when there are more than 512 replicas.  Below that the replica-resident
 // kernel (no grid barrier) is faster; above it that kernel's per-spin loop over n

@@ -62,6 +62,7 @@ SIGNATURES = {
     "nmfa_last_kernel_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
     "nmfa_measure_alu_peaks": (ctypes.c_int, [_P, _P]),
     "nmfa_tune_replicas_per_cta": (ctypes.c_int, [_P, _i32]),
+    "nmfa_debug_withhold_arrival": (ctypes.c_int, [_P, _i32]),
     "nmfa_launch_count": (_u64, []),
     "nmfa_last_error": (ctypes.c_char_p, []),
     "nmfa_version": (ctypes.c_char_p, []),
@@ -203,6 +204,10 @@ def nmfa_measure_alu_peaks(stream=None):
 
 def nmfa_tune_replicas_per_cta(handle, rc):
     _check(load().nmfa_tune_replicas_per_cta(handle, int(rc)))
+
+
+def nmfa_debug_withhold_arrival(handle, step):
+    _check(load().nmfa_debug_withhold_arrival(handle, int(step)))
 
 
 def nmfa_launch_count():

@@ -26,7 +26,8 @@ def _rand_state(R, n, seed):
 
 # ---------------------------------------------------------------- single step
 @pytest.mark.parametrize("prec", DENSE)
-@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64), (700, 130), (200, 1030)])
+@pytest.mark.parametrize("n,R", [(100, 100), (300, 200), (1, 3), (5, 7), (257, 64), (700, 130), (200, 1030),
+                                 (256, 1), (129, 600), (256, 1100)])
 def test_single_step_phi(prec, n, R):
     J = inst.sk(n, 100 + n) if n > 1 else np.zeros((1, 1))
     h = inst.random_fields(n, 0.5, 7) if prec != "bf16" else None
@@ -192,6 +193,30 @@ def test_fp32_tiled_zero_steps_keep_the_initial_state():
     g.close()
     np.testing.assert_array_equal(out["state"], s0.astype(np.float32).astype(np.float64))
     np.testing.assert_array_equal(out["signs"], np.where(s0 >= 0, 1, -1))
+
+
+def test_fp32_tiled_withheld_arrival_times_out_and_the_problem_recovers():
+    # Failure detection without a GPU fault: the first CTA of the FP32 tiled kernel
+    # leaves out its arrival at the grid barrier that closes step 3, so every CTA's
+    # bounded wait there gives up; the run reports NMFA_ETIMEOUT, and the next runs of
+    # the same problem give the results of a run before the failure.
+    from paper_1806_08422_gb300 import nmfa
+    n, R = 700, 130
+    J = inst.sk(n, 11)
+    T = inst.schedule(10)
+    g = Gpu(J, precision="fp32")
+    ref = g.run(T, 0.15, 0.15, R, seed=3, want_state=True)
+    nmfa.nmfa_debug_withhold_arrival(g.p.handle, 3)
+    with pytest.raises(nmfa.NmfaError) as ei:
+        g.run(T, 0.15, 0.15, R, seed=3, want_state=True)
+    assert ei.value.code == nmfa.NMFA_ETIMEOUT
+    nmfa.nmfa_debug_withhold_arrival(g.p.handle, -1)
+    for _ in range(2):
+        again = g.run(T, 0.15, 0.15, R, seed=3, want_state=True)
+        np.testing.assert_array_equal(again["state"], ref["state"])
+        np.testing.assert_array_equal(again["signs"], ref["signs"])
+        np.testing.assert_array_equal(again["energy_i64"], ref["energy_i64"])
+    g.close()
 
 
 @pytest.mark.parametrize("prec", DENSE)
