@@ -337,19 +337,21 @@ csr_kernel(CsrProblem pb, RunParams rp) {
 // launch.  A step is the product P = J S of the couplings with the state (spins x
 // replicas) followed by the field, Boltzmann and mixing updates of every spin.
 //
-// Tiles.  P is cut into 128-spin x 64-replica tiles.  A CTA computes a tile with a
-// register-blocked CUDA-core GEMM (8 spins x 4 replicas per thread) over 32-deep K
-// slices of J and S that cp.async copies into a three-stage shared-memory ring, so
-// the copies of later slices overlap the arithmetic on the current one.  J is
-// symmetric, so row k of J holds column k and the A slice is read by rows.
+// Tiles.  P is cut into 128-spin x 64-replica tiles.  A CTA computes a tile (or a
+// K range of one) with a register-blocked CUDA-core GEMM (8 spins x 4 replicas per
+// thread) over 32-deep K slices of J and S that cp.async copies into a three-stage
+// shared-memory ring, so the copies of later slices overlap the arithmetic on the
+// current one.  J is symmetric, so row k of J holds column k and the A slice is read
+// by rows.
 //
-// Split K.  When the tiles are fewer than half the co-resident CTAs, each tile's K
-// range is cut into `splits` ranges, one CTA each.  A range leaves its partial tile
-// in global scratch and counts itself in on the tile's counter; once all ranges of
-// the tile are in, each of its CTAs sums its share of the tile over the ranges in
-// range order (so a run is deterministic for a given split) and applies the update
-// to that share.  Without a split a CTA applies the update to its tile from
-// registers and takes the next tile.
+// Stream-K.  A step's work, tiles x K slices, is divided evenly over all co-resident
+// CTAs in one contiguous range each (tile-major), so every SM carries the same load
+// whatever the tile count.  A tile inside one range is updated from registers; a
+// tile shared by several ranges (at most a range's first and last) gets the partial
+// sums of each range in that CTA's scratch slot, and once all of its contributors
+// have counted themselves in on the tile's counter, each of them sums its share of
+// the tile over the contributions in K order (so a run is deterministic for a given
+// grid) and applies the update to that share.
 //
 // Steps.  A grid barrier (a counter that every CTA adds to and waits on) closes the
 // initialisation and every step; the state is double-buffered, S[2][n_pad][ld], so a
@@ -363,14 +365,13 @@ constexpr int kFBM = 128, kFBN = 64, kFBK = 32, kFStages = 3, kFThreads = 256;
 constexpr int kFStageFloats = kFBK * (kFBM + kFBN);
 constexpr int kFSmemBytes = kFStages * kFStageFloats * static_cast<int>(sizeof(float));
 constexpr int kFTileFloats = kFBM * kFBN;
-constexpr int kFShareMax = (kFTileFloats / 4 / 2 + kFThreads - 1) / kFThreads;  // cells a thread reduces (splits >= 2)
+constexpr int kFShareMax = (kFTileFloats / 4 / 2 + kFThreads - 1) / kFThreads;  // cells a thread reduces (>= 2 contributors)
 constexpr uint64_t kF32WaitNs = 2000000000ull;
 constexpr uint64_t kF32StartWaitNs = 20000000000ull;
 
 struct CoopF32 {
   int n, n_pad, R, ld, t_f;
   int tiles_m, tiles;        // row tiles; all tiles (row tiles x replica tiles)
-  int splits, sps;           // K ranges per tile and 32-deep slices per range
   const float* J;            // n_pad x n_pad
   const float* h32;
   const float* inv_d32;
@@ -380,7 +381,7 @@ struct CoopF32 {
   uint32_t stream;
   const double* s0;          // R x n or nullptr
   float* S;                  // 2 x n_pad x ld
-  float* part;               // tiles x splits x kFTileFloats (splits > 1)
+  float* part;               // 2 slots of kFTileFloats partial sums per CTA
   uint32_t* tile_cnt;        // tiles (zero at launch)
   uint32_t* bar;             // grid barrier counter (zero at launch)
   int8_t* signs;
@@ -409,8 +410,9 @@ __device__ __forceinline__ void coop_arrive(uint32_t* cnt) {
   __syncthreads();
   if (threadIdx.x == 0) ptx::red_release_gpu_add(cnt, 1u);
 }
-__device__ __noinline__ bool coop_wait(const uint32_t* cnt, uint32_t need, int32_t* status, uint64_t limit_ns) {
+__device__ __forceinline__ bool coop_wait(const uint32_t* cnt, uint32_t need, int32_t* status, uint64_t limit_ns) {
   __shared__ int ok;
+  __syncthreads();  // every thread has read the previous wait's verdict
   if (threadIdx.x == 0) {
     int good = 1;
     const uint64_t t0 = ptx::globaltimer_ns();
@@ -488,6 +490,13 @@ __device__ __forceinline__ void coop_gemm(const CoopF32& a, const float* cur, fl
   __syncthreads();
 }
 
+// Stream-K division of the U = tiles x slices work units of a step (unit u is K
+// slice u % slices of tile u / slices) over G CTAs: CTA c takes [U c / G, U (c + 1) / G)
+// (floors), and the CTA whose range holds unit x is ceil((x + 1) G / U) - 1.
+__device__ __forceinline__ int coop_owner(int64_t U, int G, int64_t x) {
+  return static_cast<int>(((x + 1) * G + U - 1) / U - 1);
+}
+
 // Noise of spin i for replicas r..r+3 at step t, and their state before the step.
 __device__ __forceinline__ void coop_inputs(const CoopF32& a, const float* cur, int t, int i, int r, float4& z,
                                             float4& so) {
@@ -536,16 +545,42 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
   if (!coop_wait(a.bar, phase * gridDim.x, a.status, kF32StartWaitNs)) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int slices = a.n_pad / kFBK;
+  // This CTA's work units [my0, my1) (stream-K division, fixed for the run) and the
+  // tiles it holds in part: at most its first and its last tile.  For each such tile,
+  // its contributors are CTAs lo .. lo + k - 1 in K order; contributor lo keeps its
+  // partial sums in slot 1 when the tile is its last tile (its range starts in an
+  // earlier tile), every other contributor in slot 0 (the tile is its first).
+  const int G = static_cast<int>(gridDim.x);
+  const int64_t U = static_cast<int64_t>(a.tiles) * slices;
+  const int64_t my0 = U * blockIdx.x / G, my1 = U * (blockIdx.x + 1) / G;
+  const int t_first = static_cast<int>(my0 / slices), t_last = static_cast<int>((my1 - 1) / slices);
+  int part_tile[2] = {0, 0}, part_lo[2] = {0, 0}, part_k[2] = {2, 2}, part_lo_slot[2] = {0, 0};
+  int n_part = 0;
+  for (int tile = t_first; tile <= t_last; tile += (t_last > t_first ? t_last - t_first : 1)) {
+    const int64_t tb = static_cast<int64_t>(tile) * slices;
+    if (my0 <= tb && my1 >= tb + slices) continue;  // whole tile
+    const int lo = coop_owner(U, G, tb), hi = coop_owner(U, G, tb + slices - 1);
+    part_tile[n_part] = tile;
+    part_lo[n_part] = lo;
+    part_k[n_part] = hi - lo + 1;
+    part_lo_slot[n_part] = U * lo / G < tb ? 1 : 0;
+    ++n_part;
+  }
   for (int t = 0; t < a.t_f; ++t) {
     const float* cur = a.S + (t & 1) * plane;
     float* nxt = a.S + ((t & 1) ^ 1) * plane;
     const float inv_T = static_cast<float>(1.0 / a.T[t]);
     const bool last = t == a.t_f - 1;
     float acc[8][4];
-    if (a.splits == 1) {
-      for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-        const int i0 = (tile % a.tiles_m) * kFBM, r0 = (tile / a.tiles_m) * kFBN;
-        coop_gemm(a, cur, ring, i0, r0, 0, slices, acc);
+    // (1) the range tile by tile: a whole tile is updated from registers; the part of
+    //     a shared tile leaves its partial sums in this CTA's slot and is counted in
+    for (int tile = t_first; tile <= t_last; ++tile) {
+      const int64_t tb = static_cast<int64_t>(tile) * slices;
+      const int s0 = static_cast<int>(max(my0, tb) - tb);
+      const int s1 = static_cast<int>(min(my1, tb + slices) - tb);
+      const int i0 = (tile % a.tiles_m) * kFBM, r0 = (tile / a.tiles_m) * kFBN;
+      coop_gemm(a, cur, ring, i0, r0, s0, s1, acc);
+      if (s0 == 0 && s1 == slices) {
         const int r = r0 + tx * 4;
         if (r < a.R) {
 #pragma unroll
@@ -558,47 +593,65 @@ __global__ void __launch_bounds__(kFThreads, 2) dense_f32_coop_kernel(CoopF32 a)
             }
           }
         }
+      } else {
+        const int slot = tile == t_first ? 0 : 1;
+        float* mine = a.part + (2 * static_cast<int64_t>(blockIdx.x) + slot) * kFTileFloats;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          __stcg(reinterpret_cast<float4*>(mine + (ty * 8 + m) * kFBN + tx * 4),
+                 make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]));
+        coop_arrive(a.tile_cnt + tile);
       }
-    } else if (blockIdx.x < a.tiles * a.splits) {
-      const int tile = blockIdx.x / a.splits, q = blockIdx.x % a.splits;
+    }
+    // (2) the shared tiles: once all contributors are in, this CTA (contributor jme of
+    //     k) sums its share of the tile's float4 cells over the contributions in K
+    //     order and applies the update to it (k >= 2, so at most kFShareMax cells a thread)
+#pragma unroll
+    for (int pt = 0; pt < 2; ++pt) {
+      if (pt >= n_part) break;
+      const int tile = part_tile[pt], lo_c = part_lo[pt], k = part_k[pt];
       const int i0 = (tile % a.tiles_m) * kFBM, r0 = (tile / a.tiles_m) * kFBN;
-      const int s0 = q * a.sps, s1 = min(slices, s0 + a.sps);
-      coop_gemm(a, cur, ring, i0, r0, s0, s1, acc);
-      float* mine = a.part + (static_cast<int64_t>(tile) * a.splits + q) * kFTileFloats;
-#pragma unroll
-      for (int m = 0; m < 8; ++m)
-        __stcg(reinterpret_cast<float4*>(mine + (ty * 8 + m) * kFBN + tx * 4),
-               make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]));
-      coop_arrive(a.tile_cnt + tile);
-      // this CTA's share of the tile, float4 cells [lo, hi) of its 128 x 16 grid (at
-      // most kFShareMax a thread, as splits >= 2): noise and old state are fetched
-      // while the other K ranges of the tile come in
-      const int per = (kFTileFloats / 4 + a.splits - 1) / a.splits;
-      const int lo = q * per, hi = min(kFTileFloats / 4, lo + per);
-      float4 zq[kFShareMax], sq[kFShareMax];
-#pragma unroll
-      for (int j = 0; j < kFShareMax; ++j) {
-        const int e = lo + threadIdx.x + kFThreads * j;
+      const int per = (kFTileFloats / 4 + k - 1) / k;
+      const int clo = (static_cast<int>(blockIdx.x) - lo_c) * per, chi = min(kFTileFloats / 4, clo + per);
+      // the noise and old state of the thread's first cell (its only one once a tile
+      // has 8 or more contributors) are fetched while the other contributions come in
+      float4 z0, so0;
+      {
+        const int e = clo + threadIdx.x;
         const int i = i0 + (e >> 4), r = r0 + (e & 15) * 4;
-        if (e < hi && i < n && r < a.R) coop_inputs(a, cur, t, i, r, zq[j], sq[j]);
+        if (e < chi && i < n && r < a.R) coop_inputs(a, cur, t, i, r, z0, so0);
       }
-      if (!coop_wait(a.tile_cnt + tile, static_cast<uint32_t>(t + 1) * a.splits, a.status, kF32WaitNs)) return;
-      const float* base = a.part + static_cast<int64_t>(tile) * a.splits * kFTileFloats;
+      if (!coop_wait(a.tile_cnt + tile, static_cast<uint32_t>(t + 1) * k, a.status, kF32WaitNs)) return;
 #pragma unroll
       for (int j = 0; j < kFShareMax; ++j) {
-        const int e = lo + threadIdx.x + kFThreads * j;
-        const int row = e >> 4, c4 = e & 15;
-        const int i = i0 + row, r = r0 + c4 * 4;
-        if (e >= hi || i >= n || r >= a.R) continue;
+        const int e = clo + threadIdx.x + kFThreads * j;
+        const int i = i0 + (e >> 4), r = r0 + (e & 15) * 4;
+        if (e >= chi || i >= n || r >= a.R) continue;
+        const float* cell = a.part + (e >> 4) * kFBN + (e & 15) * 4;
+        // contributions in K order, four loads in flight at a time
         float P[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int qq = 0; qq < a.splits; ++qq) {
-          const float4 v = __ldcg(reinterpret_cast<const float4*>(base + qq * kFTileFloats + row * kFBN + c4 * 4));
-          P[0] += v.x;
-          P[1] += v.y;
-          P[2] += v.z;
-          P[3] += v.w;
+        for (int c0 = lo_c; c0 < lo_c + k; c0 += 4) {
+          float4 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u;
+            if (c < lo_c + k)
+              v[u] = __ldcg(reinterpret_cast<const float4*>(
+                  cell + (2 * static_cast<int64_t>(c) + (c == lo_c ? part_lo_slot[pt] : 0)) * kFTileFloats));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (c0 + u < lo_c + k) {
+              P[0] += v[u].x;
+              P[1] += v[u].y;
+              P[2] += v[u].z;
+              P[3] += v[u].w;
+            }
+          }
         }
-        coop_apply(a, nxt, inv_T, i, r, P, zq[j], sq[j], last);
+        float4 z = z0, so = so0;
+        if (j > 0) coop_inputs(a, cur, t, i, r, z, so);
+        coop_apply(a, nxt, inv_T, i, r, P, z, so, last);
       }
     }
     ++phase;
@@ -729,10 +782,10 @@ int coop_f32_capacity() {
   return cap;
 }
 
-// Tiles, K split and scratch layout of one run: [state 2 x n_pad x ld floats]
-// [partial tiles, when split][tile counters, grid barrier counter].
+// Tiles, grid and scratch layout of one run: [state 2 x n_pad x ld floats]
+// [2 partial-tile slots per CTA][tile counters, grid barrier counter].
 struct CoopF32Plan {
-  int n_pad, ld, tiles_m, tiles, splits, sps, grid;
+  int n_pad, ld, tiles_m, tiles, grid;
   int64_t state_floats, part_floats, cnt_words;
   int64_t bytes() const { return 4 * (state_floats + part_floats + cnt_words); }
 };
@@ -744,15 +797,20 @@ CoopF32Plan plan_coop_f32(int n, int R) {
   pl.tiles_m = pl.n_pad / kFBM;
   pl.tiles = pl.tiles_m * (pl.ld / kFBN);
   const int slices = pl.n_pad / kFBK;
+  // Grid: while the tiles fill at most half of the co-resident CTAs, each tile is
+  // cut into `splits` equal K ranges (splits the largest divisor of the slice count
+  // that fits), so that every range lies in one tile; otherwise every co-resident
+  // CTA, whose ranges then cross tile boundaries and even out the load.
   const int cap = coop_f32_capacity();
-  // Split K only while the tiles fill at most half of the co-resident CTAs; ranges
-  // of equal length (the last one shorter), none empty.
-  pl.splits = 2 * pl.tiles <= cap ? std::min(slices, cap / pl.tiles) : 1;
-  pl.sps = (slices + pl.splits - 1) / pl.splits;
-  pl.splits = (slices + pl.sps - 1) / pl.sps;
-  pl.grid = pl.splits > 1 ? pl.tiles * pl.splits : std::min(pl.tiles, cap);
+  if (2 * pl.tiles <= cap) {
+    int splits = std::min(slices, cap / pl.tiles);
+    while (slices % splits != 0) --splits;
+    pl.grid = pl.tiles * splits;
+  } else {
+    pl.grid = cap;
+  }
   pl.state_floats = 2ll * pl.n_pad * pl.ld;
-  pl.part_floats = pl.splits > 1 ? static_cast<int64_t>(pl.tiles) * pl.splits * kFTileFloats : 0;
+  pl.part_floats = 2ll * pl.grid * kFTileFloats;
   pl.cnt_words = (pl.tiles + 1 + 63) / 64 * 64;
   return pl;
 }
@@ -766,7 +824,7 @@ int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void
   const int n = pb.n, R = rp.replicas;
   const CoopF32Plan pl = plan_coop_f32(n, R);
   if (pb.ldj != pl.n_pad) return set_error(NMFA_EINVAL, "tiled FP32 path: J is not stored n_pad x n_pad");
-  // the barrier counter reaches (t_f + 1) x grid and the tile counters t_f x splits
+  // the barrier counter reaches (t_f + 1) x grid and a tile counter at most t_f x grid
   if ((static_cast<int64_t>(rp.t_f) + 1) * pl.grid >= (int64_t(1) << 32))
     return set_error(NMFA_EUNSUPPORTED, "tiled FP32 path: t_f too large for the step counters");
   CoopF32 a{};
@@ -777,8 +835,6 @@ int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void
   a.t_f = rp.t_f;
   a.tiles_m = pl.tiles_m;
   a.tiles = pl.tiles;
-  a.splits = pl.splits;
-  a.sps = pl.sps;
   a.J = static_cast<const float*>(pb.J);
   a.h32 = static_cast<const float*>(pb.h);
   a.inv_d32 = pb.inv_d32;
@@ -801,7 +857,7 @@ int launch_dense_tiled_f32(const DenseSimtProblem& pb, const RunParams& rp, void
   int rc = cuda_error(cudaMemsetAsync(a.tile_cnt, 0, 4 * pl.cnt_words, st), "tiled FP32 counters");
   if (rc) return rc;
   // cooperative: every CTA is resident at once (the CTAs wait on one another at
-  // the grid barrier and the split tiles' counters)
+  // the grid barrier and the shared tiles' counters)
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(pl.grid);
   cfg.blockDim = dim3(kFThreads);

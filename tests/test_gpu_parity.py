@@ -129,9 +129,12 @@ def test_second_step_reads_every_row_blocks_first_step_state(n, R):
 
 # Five-step cases: the tensor path (64-replica tiles over 3 row blocks; 128-replica
 # tiles over 9 row blocks with a ragged tail) and the FP32 tiled kernel (n >= 256,
-# 128-spin x 64-replica tiles; its K split depends on the co-resident CTAs, here for
-# 152 SMs x 2): 18 tiles cut into 12 K ranges, 90 tiles into 3, 216 tiles one per CTA,
-# and 320 tiles, two for some CTAs.
+# 128-spin x 64-replica tiles of 32-deep K slices; here for 152 SMs x 2 co-resident
+# CTAs): 18 tiles of 24 slices, each cut into 12 K ranges of 2; 90 tiles of 36 cut
+# into 3 ranges of 12; and, once the tiles outnumber half the CTAs, the tiles x
+# slices divided evenly over all 304 CTAs across tile boundaries: 216 tiles of 48
+# (34 slices a CTA) and 320 tiles of 80 (84: most CTAs hold a whole tile besides
+# parts of its neighbours).
 FIVE_STEP_CASES = [("bf16", 384, 200), ("bf16", 1100, 256), ("fp32", 700, 130), ("fp32", 1100, 600),
                    ("fp32", 1500, 1100), ("fp32", 2500, 1000)]
 
