@@ -356,7 +356,7 @@ def leg_served(rate=200.0, duration=0.5, n_lo=64, n_hi=2048, fp32_cap=30.0):
                         % (rate, duration, len(reqs), n_lo, n_hi),
             "tensor_server": dict(summary(srv, srv["requests"]), launches=srv["launches"],
                                   batches_reused=srv["batches_reused"],
-                                  mean_attempts=srv["mean_attempts"], precision="FP8-E4M3-stored J, BF16 S"),
+                                  mean_attempts=srv["mean_attempts"], precision="FP8-E4M3-stored J (widened to BF16 once per batch for N <= 4096), BF16 S"),
             "tensor_server_bf16_stored_j": dict(summary(srv16, srv16["requests"]), launches=srv16["launches"],
                                                 batches_reused=srv16["batches_reused"]),
             "fp32_per_instance": dict(summary(f32, f32["served"]), time_cap_s=fp32_cap,

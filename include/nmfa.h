@@ -61,7 +61,9 @@ typedef enum {
                          BF16 in shared memory, so runs are bit-identical to NMFA_BF16
                          runs of the same J; the conversion costs time where J fits
                          in L2 (about 1.1x the step time with 256-replica tiles,
-                         1.5x with 128-replica tiles, measured on GB300) */
+                         1.5x with 128-replica tiles, measured on GB300), so batches
+                         widen problems of n <= 4096 once instead (see
+                         NMFA_BATCH_FP8_IN_KERNEL) */
 } nmfa_precision;
 
 typedef struct nmfa_problem nmfa_problem; /* opaque; owns device copies of (h, J) */
@@ -230,6 +232,14 @@ typedef struct nmfa_batch nmfa_batch;
  * results agree with one-CTA tiles to the BF16 path's rounding rather than bit for
  * bit; pair runs are still independent of what else a batch holds. */
 #define NMFA_BATCH_PAIR128 32
+/* FP8-stored problems (NMFA_BF16_FP8J) of n rounded to 128 up to 4096 are by default
+ * widened to BF16 once, at batch creation, into a scratch copy of 2 x n_pad^2 bytes
+ * held by the batch (it counts in nmfa_batch_info's workspace bytes), and run on the
+ * BF16 kernel: the in-kernel widening of every staged slice costs 1.2-1.6x the step
+ * time at those sizes on GB300, while the copy is at most 32 MB.  Larger FP8 problems
+ * are read as stored and widened in the kernel.  With this option every FP8 problem
+ * of the batch is read as stored.  Results do not change. */
+#define NMFA_BATCH_FP8_IN_KERNEL 128
 /* Test only: leave the first group's last row-block tile out of the plan.  Nothing
  * then publishes that tile's state, so the group's other tiles wait for a flag that
  * is never set: their bounded waits give up (within 2 s, 20 s at most),

@@ -1147,9 +1147,38 @@ __global__ void convert_dense_kernel(int n, const double* __restrict__ J64, void
   }
 }
 
+// E4M3 couplings as stored (each group of four in the order k0, k2, k1, k3) to BF16
+// in the natural order; exact (every finite E4M3 value is a BF16 value).
+__global__ void widen_e4m3_kernel(const uint32_t* __restrict__ src, uint2* __restrict__ dst, int64_t words) {
+  for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < words;
+       w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t v = src[w];
+    __nv_bfloat16 o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_fp8_e4m3 x;
+      x.__x = static_cast<__nv_fp8_storage_t>((v >> (8 * q)) & 0xFFu);
+      o[q == 1 ? 2 : q == 2 ? 1 : q] = __float2bfloat16_rn(static_cast<float>(x));
+    }
+    uint2 out;
+    out.x = static_cast<uint32_t>(__bfloat16_as_ushort(o[0])) | (static_cast<uint32_t>(__bfloat16_as_ushort(o[1])) << 16);
+    out.y = static_cast<uint32_t>(__bfloat16_as_ushort(o[2])) | (static_cast<uint32_t>(__bfloat16_as_ushort(o[3])) << 16);
+    dst[w] = out;
+  }
+}
+
 __global__ void convert_vec_kernel(int n, const double* __restrict__ src, void* dst, int kind) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) store_kind(dst, i, src != nullptr ? src[i] : 0.0, kind);
+}
+
+int launch_widen_e4m3(const void* Jq8, void* Jq16, int64_t n_pad, cudaStream_t st) {
+  const int64_t words = n_pad * n_pad / 4;
+  const int grid = static_cast<int>(std::min<int64_t>((words + 255) / 256, 4096));
+  widen_e4m3_kernel<<<std::max(grid, 1), 256, 0, st>>>(static_cast<const uint32_t*>(Jq8), static_cast<uint2*>(Jq16),
+                                                        words);
+  count_launch();
+  return cuda_error(cudaGetLastError(), "E4M3 widening kernel launch");
 }
 
 int launch_row_norms_dense(int32_t n, const double* J64, const double* h, double* d, float* inv_d32,

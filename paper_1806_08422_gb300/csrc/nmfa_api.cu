@@ -959,6 +959,7 @@ struct nmfa_batch {
   std::vector<nmfa_job> jobs;
   std::vector<int> bn;
   std::vector<DevBuf> ws;   // one workspace per plan
+  std::vector<DevBuf> widened;  // BF16 copies of FP8-stored problems widened once (one per problem)
   DevBuf signs;             // sign scratch for jobs that did not supply a buffer
   std::vector<int8_t*> signs_ptr;
   std::vector<char> energy_fused;  // per job: energies formed inside the persistent kernel
@@ -985,6 +986,7 @@ static void free_batch(nmfa_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (DevBuf& w : b->ws) pool_free(w.p);
+  for (DevBuf& w : b->widened) pool_free(w.p);
   pool_free(b->signs.p);
   pool_free(b->status);
   if (b->done) cudaEventDestroy(b->done);
@@ -1072,6 +1074,7 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
   std::vector<TcJob> tj(count);
   size_t sp = 0;
   b->signs_ptr.resize(count);
+  std::vector<const nmfa_problem*> widened_of;  // the problem each widened copy belongs to
   for (int32_t j = 0; j < count; ++j) {
     nmfa_problem* p = problems[j];
     const nmfa_job& jb = jobs[j];
@@ -1086,6 +1089,20 @@ int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32
     t.pb.n_pad = p->n_pad;
     t.pb.Jq = p->Jq;
     t.pb.fp8 = p->precision == NMFA_BF16_FP8J;  // read as stored (E4M3), widened to BF16 in the kernel
+    if (t.pb.fp8 && p->n_pad <= kFp8WidenOnceMaxNpad && !(options & NMFA_BATCH_FP8_IN_KERNEL)) {
+      // small and mid-size FP8 problems: one BF16 copy per problem for the batch's
+      // lifetime, and the BF16 kernel (bit-identical runs)
+      size_t w = 0;
+      while (w < widened_of.size() && widened_of[w] != p) ++w;
+      if (w == widened_of.size()) {
+        b->widened.emplace_back();
+        if ((rc = ensure_buf(b->widened.back(), 2 * static_cast<size_t>(p->n_pad) * p->n_pad))) return fail(rc);
+        if ((rc = launch_widen_e4m3(p->Jq, b->widened.back().p, p->n_pad, b->own))) return fail(rc);
+        widened_of.push_back(p);
+      }
+      t.pb.Jq = b->widened[w].p;
+      t.pb.fp8 = false;
+    }
     t.pb.inv_d32 = p->inv_d32;
     t.pb.h32 = p->h32;
     t.pb.energy_exact = p->energy_exact;
@@ -1243,6 +1260,7 @@ int nmfa_batch_info(const nmfa_batch* b, int32_t* grid, int32_t* groups, int64_t
   if (workspace_bytes) {
     size_t tot = b->signs.bytes;
     for (const DevBuf& w : b->ws) tot += w.bytes;
+    for (const DevBuf& w : b->widened) tot += w.bytes;
     *workspace_bytes = static_cast<int64_t>(tot);
   }
   return NMFA_OK;

@@ -125,6 +125,15 @@ int launch_row_norms_csr(int32_t n, const int32_t* row_ptr, const double* val64,
 // rows x ld.  kind: 0 = float, 1 = bf16, 2 = e4m3, 3 = int8.
 int launch_convert_dense(int32_t n, const double* J64, void* dst, int kind, int64_t rows,
                          int64_t ld, cudaStream_t st);
+// BF16 n_pad x n_pad couplings (natural order) from their E4M3 storage (each group of
+// four values stored as k0, k2, k1, k3); exact.
+int launch_widen_e4m3(const void* Jq8, void* Jq16, int64_t n_pad, cudaStream_t st);
+// FP8-stored problems up to this n_pad are widened to BF16 once per batch (a scratch
+// copy of 2 n_pad^2 bytes) instead of slice by slice in the kernel every step: the
+// kernel's converter warps cost 1.2-1.6x the step time there (measured on GB300,
+// SK, 200 steps: n = 1024, R = 512 1.19x; n = 2000, R = 1024 1.45x; n = 4096, R = 512
+// 1.58x), while the copy is at most 32 MB.  Larger problems are read as stored.
+constexpr int32_t kFp8WidenOnceMaxNpad = 4096;
 int launch_convert_vec(int32_t n, const double* src, void* dst, int kind, cudaStream_t st);
 
 // ---- tcgen05 tensor path ------------------------------------------------------

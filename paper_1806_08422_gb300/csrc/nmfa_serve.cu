@@ -104,19 +104,22 @@ struct nmfa_server {
 
 namespace {
 
-// Device memory a request holds while admitted: its couplings as stored (FP8-stored
-// J is read as stored by the kernel), the creation-time FP64 copy, the tensor
-// kernel's scratch and its inputs/outputs.  The state is counted for the widest tile
+// Device memory a request holds while admitted: its couplings as stored, the BF16
+// copy a batch makes of FP8-stored couplings of n_pad <= 4096 (larger ones are read
+// as stored by the kernel), the creation-time FP64 copy, the tensor kernel's scratch
+// and its inputs/outputs.  The state is counted for the widest tile
 // the library may pick (256 replicas), so admission never under-counts it.
 int64_t request_footprint(const Request* r) {
   const int64_t n = r->n, n_pad = (n + 127) / 128 * 128;
   const int64_t bn = r->replicas <= 64 ? 64 : 256;
   const int64_t r_pad = (r->replicas + bn - 1) / bn * bn;
   const int64_t jq = (r->precision == NMFA_BF16 ? 2 : 1) * n_pad * n_pad;
+  // FP8-stored couplings of small and mid-size problems are widened once per batch
+  const int64_t widened = (r->precision == NMFA_BF16_FP8J && n_pad <= kFp8WidenOnceMaxNpad) ? 2 * n_pad * n_pad : 0;
   const int64_t creation = 8 * n * n;                      // FP64 staging copy held by the problem
   const int64_t scratch = 4 * r_pad * n_pad + (1 << 20);
   const int64_t io = r->replicas * (n + 16) + 8 * r->t_f;
-  return jq + n * n + creation + scratch + io;
+  return jq + widened + n * n + creation + scratch + io;
 }
 
 // Finished requests are handed to the reaper thread, which destroys their problems

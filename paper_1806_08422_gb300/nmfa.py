@@ -236,6 +236,7 @@ NMFA_BATCH_BN128 = 16
 NMFA_BATCH_PAIR128 = 32
 NMFA_BATCH_BN256 = 64
 NMFA_BATCH_DEBUG_WITHHOLD_TILE = 8
+NMFA_BATCH_FP8_IN_KERNEL = 128
 
 
 def make_job(T_dev, sigma, alpha, replicas, seed=0, stream_id=0, signs=None, energy=None, energy_i64=None):

@@ -131,7 +131,8 @@ def main():
     ap.add_argument("--t-f", type=int, default=1000)
     ap.add_argument("--max-inflight", type=int, default=2)
     ap.add_argument("--precision", default="bf16_fp8j", choices=["bf16", "bf16_fp8j"],
-                    help="storage of J: bf16, or bf16_fp8j (E4M3, half the bytes, converted in the kernel)")
+                    help="storage of J: bf16, or bf16_fp8j (E4M3, half the bytes; batches widen n <= 4096 once, "
+                         "larger n in the kernel)")
     ap.add_argument("--fp32-cap", type=float, default=30.0, help="seconds of FP32 FIFO serving (0: skip)")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()

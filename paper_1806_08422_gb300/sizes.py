@@ -43,6 +43,9 @@ def time_one(J, R, t_f, storage, reps, options=0):
     s = torch.empty((R, n), dtype=torch.int8, device=dev)
     e = torch.empty(R, dtype=torch.int64, device=dev)
     st = torch.cuda.Stream()
+    # FP8 storage: the kernel's own widening (batches would widen n <= 4096 once)
+    if storage == "bf16_fp8j":
+        options |= nmfa.NMFA_BATCH_FP8_IN_KERNEL
     b = nmfa.nmfa_batch_create([p.handle], [nmfa.make_job(T, 0.15, 0.15, R, signs=s, energy_i64=e)], options)
     try:
         nmfa.nmfa_batch_launch(b, st)  # warm-up

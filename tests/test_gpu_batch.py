@@ -146,9 +146,11 @@ def _e4m3_exact_couplings(n, seed):
 @pytest.mark.parametrize("n,R,tf", [(300, 192, 60), (1000, 64, 40), (2048, 2048, 20)])
 def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
     # FP8-stored couplings reach the tensor cores through the kernel's converter warps
-    # (E4M3 slice -> BF16 operand in shared memory); the run equals the same couplings
-    # stored in BF16 bit for bit, for every exact E4M3 value; both storages take the
-    # same tile widths (64, 64 and 256 here), and a forced 128 gives the same run.
+    # (E4M3 slice -> BF16 operand in shared memory; single runs, and batches with
+    # NMFA_BATCH_FP8_IN_KERNEL); the run equals the same couplings stored in BF16 bit
+    # for bit, for every exact E4M3 value; both storages take the same tile widths
+    # (64, 64 and 256 here), and a forced 128 gives the same run.  A default batch
+    # widens these sizes once to BF16 and equals them too.
     torch, dev = _dev()
     from paper_1806_08422_gb300 import nmfa
     J = _e4m3_exact_couplings(n, 40 + n)
@@ -161,7 +163,7 @@ def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
         sb = torch.empty((R, n), dtype=torch.int8, device=dev)
         eb = torch.empty(R, dtype=torch.float64, device=dev)  # real-valued couplings: FP64 energies
         b = nmfa.nmfa_batch_create([p.handle], [nmfa.make_job(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=sb,
-                                                              energy=eb)], 0)
+                                                              energy=eb)], nmfa.NMFA_BATCH_FP8_IN_KERNEL)
         res[name + "_plan"] = nmfa.nmfa_batch_plan(b)
         nmfa.nmfa_batch_launch(b)
         nmfa.nmfa_batch_sync(b)
@@ -177,7 +179,8 @@ def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
         sb = torch.empty((R, n), dtype=torch.int8, device=dev)
         eb = torch.empty(R, dtype=torch.float64, device=dev)
         b = nmfa.nmfa_batch_create([f.handle], [nmfa.make_job(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=sb,
-                                                              energy=eb)], nmfa.NMFA_BATCH_BN128)
+                                                              energy=eb)],
+                                   nmfa.NMFA_BATCH_BN128 | nmfa.NMFA_BATCH_FP8_IN_KERNEL)
         assert nmfa.nmfa_batch_plan(b) == [(128, 1, 1)]
         nmfa.nmfa_batch_launch(b)
         nmfa.nmfa_batch_sync(b)
@@ -189,6 +192,15 @@ def test_fp8_converted_in_kernel_matches_bf16(n, R, tf):
     np.testing.assert_array_equal(res["fp8"][0], res["bf16"][0])
     np.testing.assert_array_equal(res["fp8"][1], res["bf16"][1])
     np.testing.assert_array_equal(res["fp8_batch"][0], res["fp8"][0])  # batched = alone
+    sb = torch.empty((R, n), dtype=torch.int8, device=dev)
+    eb = torch.empty(R, dtype=torch.float64, device=dev)
+    b = nmfa.nmfa_batch_create([f.handle], [nmfa.make_job(T, 0.15, 0.15, R, seed=9, stream_id=1, signs=sb,
+                                                          energy=eb)], 0)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    nmfa.nmfa_batch_destroy(b)
+    np.testing.assert_array_equal(sb.cpu().numpy(), res["bf16"][0])
+    np.testing.assert_array_equal(eb.cpu().numpy(), res["bf16"][1])
     for r in (0, R - 1):
         assert abs(res["fp8"][1][r] - oracle.energy(J, res["fp8"][0][r])) <= 1e-12 * np.abs(np.triu(J, 1)).sum()
     a.close()
@@ -212,6 +224,52 @@ def test_mixed_precision_and_width_batch():
         np.testing.assert_array_equal(e.cpu().numpy(), ea)
     nmfa.nmfa_batch_destroy(b)
     for p in problems:
+        p.close()
+
+
+def test_fp8_problems_widened_once_per_batch():
+    # FP8-stored problems of n_pad <= 4096 are widened to BF16 once, at batch
+    # creation: the batch holds a BF16 copy per problem (2 n_pad^2 bytes of its
+    # workspace, one copy for two jobs of the same problem), their jobs share the BF16
+    # launch of their tile width with BF16-stored problems, and every run equals its
+    # solo run; an FP8 problem above n_pad = 4096 is read as stored (no copy).
+    torch, dev = _dev()
+    from paper_1806_08422_gb300 import nmfa
+    T = torch.as_tensor(inst.schedule(30), device=dev)
+    J1, J2 = inst.sk(1000, 91), inst.sk(300, 92)
+    problems = [nmfa.Problem(J1, precision="bf16_fp8j"), nmfa.Problem(J1, precision="bf16"),
+                nmfa.Problem(J2, precision="bf16_fp8j")]
+    jobs = [(problems[0], (T, 256, 5, 0)), (problems[1], (T, 256, 5, 0)), (problems[0], (T, 256, 6, 1)),
+            (problems[2], (T, 256, 7, 2))]
+    alone = [_alone(p, *sp) for p, sp in jobs]
+    # one tile width (64 replicas) for every job, so the launches are per storage only
+    b, outs = _batch([p for p, _ in jobs], [sp for _, sp in jobs], nmfa.NMFA_BATCH_BN64)
+    assert len(nmfa.nmfa_batch_plan(b)) == 1  # one launch: the FP8 jobs run on the BF16 kernel
+    ws = nmfa.nmfa_batch_info(b)["workspace_bytes"]
+    b_in, _ = _batch([p for p, _ in jobs], [sp for _, sp in jobs],
+                     nmfa.NMFA_BATCH_BN64 | nmfa.NMFA_BATCH_FP8_IN_KERNEL)
+    assert len(nmfa.nmfa_batch_plan(b_in)) == 2
+    assert ws >= 2 * (1024 * 1024 + 384 * 384) + nmfa.nmfa_batch_info(b_in)["workspace_bytes"] - (1 << 20)
+    nmfa.nmfa_batch_destroy(b_in)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    for (s, e), (sa, ea) in zip(outs, alone):
+        np.testing.assert_array_equal(s.cpu().numpy(), sa)
+        np.testing.assert_array_equal(e.cpu().numpy(), ea)
+    np.testing.assert_array_equal(outs[0][0].cpu().numpy(), outs[1][0].cpu().numpy())  # FP8 = BF16 storage
+    nmfa.nmfa_batch_destroy(b)
+    big = nmfa.Problem(inst.sk(4200, 93), precision="bf16_fp8j")
+    b, outs = _batch([big], [(T, 64, 8, 0)], 0)
+    b_in, _ = _batch([big], [(T, 64, 8, 0)], nmfa.NMFA_BATCH_FP8_IN_KERNEL)
+    assert nmfa.nmfa_batch_info(b)["workspace_bytes"] == nmfa.nmfa_batch_info(b_in)["workspace_bytes"]
+    nmfa.nmfa_batch_destroy(b_in)
+    nmfa.nmfa_batch_launch(b)
+    nmfa.nmfa_batch_sync(b)
+    s, e = _alone(big, T, 64, 8, 0)
+    np.testing.assert_array_equal(outs[0][0].cpu().numpy(), s)
+    np.testing.assert_array_equal(outs[0][1].cpu().numpy(), e)
+    nmfa.nmfa_batch_destroy(b)
+    for p in problems + [big]:
         p.close()
 
 
@@ -314,7 +372,7 @@ def test_variant_launches_side_by_side_or_in_turn(options):
         problems = [nmfa.Problem(J, precision=pr) for J, pr, _ in defs]
         specs = [(T, R, 60 + k, k) for k, (_, _, R) in enumerate(defs)]
         alone = [_alone(p, *sp) for p, sp in zip(problems, specs)]
-        b, outs = _batch(problems, specs, options)
+        b, outs = _batch(problems, specs, options | nmfa.NMFA_BATCH_FP8_IN_KERNEL)
         assert len(nmfa.nmfa_batch_plan(b)) == len(defs)
         nmfa.nmfa_batch_launch(b)
         nmfa.nmfa_batch_sync(b)

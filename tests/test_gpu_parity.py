@@ -335,8 +335,9 @@ def test_real_valued_energies_fp64(prec):
 
 # ---------------------------------------------------------------- invariants
 @pytest.mark.parametrize("prec", DENSE)
-def test_noise_negation_symmetry_gpu(prec):
-    n, R = 200, 32
+@pytest.mark.parametrize("n", [200, 300])  # FP32: the replica-resident and the tiled kernel
+def test_noise_negation_symmetry_gpu(prec, n):
+    R = 32
     J = inst.sk(n, 15)
     T = inst.schedule(100)
     g = Gpu(J, precision=prec)
@@ -348,8 +349,9 @@ def test_noise_negation_symmetry_gpu(prec):
 
 
 @pytest.mark.parametrize("prec", DENSE)
-def test_zero_state_and_state_bound(prec):
-    n, R = 130, 20
+@pytest.mark.parametrize("n", [130, 300])  # FP32: the replica-resident and the tiled kernel
+def test_zero_state_and_state_bound(prec, n):
+    R = 20
     J = inst.sk(n, 16)
     g = Gpu(J, precision=prec)
     out = g.run(inst.schedule(30), 0.0, 0.15, R, want_state=True)
