@@ -344,9 +344,12 @@ csr_kernel(CsrProblem pb, RunParams rp) {
 // current one.  J is symmetric, so row k of J holds column k and the A slice is read
 // by rows.
 //
-// Stream-K.  A step's work, tiles x K slices, is divided evenly over all co-resident
-// CTAs in one contiguous range each (tile-major), so every SM carries the same load
-// whatever the tile count.  A tile inside one range is updated from registers; a
+// Stream-K.  A step's work, tiles x K slices, is divided evenly over the grid in one
+// contiguous range per CTA (tile-major).  The grid is every co-resident CTA once the
+// tiles fill more than half of them (ranges then cross tile boundaries and every SM
+// carries the same load); below that it is tiles x splits CTAs with splits dividing
+// the slice count, so that each range is an equal K range of one tile.  A tile
+// inside one range is updated from registers; a
 // tile shared by several ranges (at most a range's first and last) gets the partial
 // sums of each range in that CTA's scratch slot, and once all of its contributors
 // have counted themselves in on the tile's counter, each of them sums its share of
@@ -412,7 +415,7 @@ __device__ __forceinline__ void coop_arrive(uint32_t* cnt) {
 }
 __device__ __forceinline__ bool coop_wait(const uint32_t* cnt, uint32_t need, int32_t* status, uint64_t limit_ns) {
   __shared__ int ok;
-  __syncthreads();  // every thread has read the previous wait's verdict
+  __syncthreads();  // every thread has read the previous wait's outcome
   if (threadIdx.x == 0) {
     int good = 1;
     const uint64_t t0 = ptx::globaltimer_ns();
