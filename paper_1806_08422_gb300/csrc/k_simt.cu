@@ -13,6 +13,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "nmfa_device.cuh"
@@ -771,18 +772,24 @@ int pick_rc_csr(int n, int replicas, size_t elem, int requested) {
   return rc;
 }
 
-// Co-resident CTAs of the cooperative FP32 kernel on the current device.
+// Co-resident CTAs of the cooperative FP32 kernel on the current device (cached per
+// device; the attribute is set on each device before its first query).
 int coop_f32_capacity() {
-  static int cap = -1;
-  if (cap < 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cap[kMaxDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+  int c = cap[slot].load(std::memory_order_relaxed);
+  if (c <= 0) {
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(dense_f32_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemBytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_f32_coop_kernel, kFThreads, kFSmemBytes);
-    cap = std::max(1, sms * per);
+    c = std::max(1, sms * per);
+    cap[slot].store(c, std::memory_order_relaxed);
   }
-  return cap;
+  return c;
 }
 
 // Tiles, grid and scratch layout of one run: [state 2 x n_pad x ld floats]
