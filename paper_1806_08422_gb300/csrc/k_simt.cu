@@ -809,11 +809,15 @@ CoopF32Plan plan_coop_f32(int n, int R) {
   const int slices = pl.n_pad / kFBK;
   // Grid: while the tiles fill at most half of the co-resident CTAs, each tile is
   // cut into `splits` equal K ranges (splits the largest divisor of the slice count
-  // that fits), so that every range lies in one tile; otherwise every co-resident
-  // CTA, whose ranges then cross tile boundaries and even out the load.
+  // that fits, at most 16), so that every range lies in one tile; otherwise every
+  // co-resident CTA, whose ranges then cross tile boundaries and even out the load.
+  // More than 16 ranges cost more in the tile's sums and counter than they save in
+  // the product (measured on GB300, 1000-step runs, n = 1024, R = 64: 32 ranges of
+  // one slice 11.3 ms, 16 of two 8.7 ms, 8 of four 11.9 ms; n = 512, R = 64: 16 of one
+  // 7.5 ms, 8 of two 8.4 ms).
   const int cap = coop_f32_capacity();
   if (2 * pl.tiles <= cap) {
-    int splits = std::min(slices, cap / pl.tiles);
+    int splits = std::min(std::min(slices, 16), cap / pl.tiles);
     while (slices % splits != 0) --splits;
     pl.grid = pl.tiles * splits;
   } else {
