@@ -354,8 +354,12 @@ int nmfa_problem_info(const nmfa_problem* p, int32_t* n, int32_t* precision,
 int nmfa_profile_enable(nmfa_problem* p, int32_t on);
 int nmfa_last_kernel_ms(nmfa_problem* p, float* ms);
 
-/* Tuning of the CUDA-core paths: replicas held by one CTA (0 = automatic, else
- * 1, 2, 4 or 8).  Results do not depend on it. */
+/* Tuning of the CUDA-core paths: replicas held by one CTA of the replica-resident
+ * kernels (0 = automatic, else 1, 2, 4 or 8).  Results do not depend on it, with one
+ * exception: a nonzero value also sends FP32 dense problems that would take the tiled
+ * kernel (n >= 256, or n > 128 with more than 512 replicas) to the replica-resident
+ * one, whose coupling sums round in another order (the results agree within the FP32
+ * path's tolerance); that kernel needs the state of n spins to fit in shared memory. */
 int nmfa_tune_replicas_per_cta(nmfa_problem* p, int32_t replicas_per_cta);
 
 /* nmfa_debug_withhold_arrival -- test entry (not part of the stable ABI), for
