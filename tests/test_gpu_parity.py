@@ -45,6 +45,27 @@ def test_single_step_phi(prec, n, R):
     g.close()
 
 
+@pytest.mark.parametrize("prec,n,R", [("fp64", 300, 40), ("fp32", 300, 40), ("fp32", 700, 130)])
+def test_single_step_real_couplings_and_field(prec, n, R):
+    # Real-valued couplings (density 0.7) and fields on the CUDA-core paths (FP32 at
+    # these sizes: the tiled kernel, 12 K ranges a tile at n = 700): Phi and the new
+    # state after one step against the oracle's
+    J = inst.random_real_couplings(n, 50 + n, density=0.7)
+    h = inst.random_fields(n, 0.7, 51)
+    sigma, alpha, seed, stream = 0.15, 0.15, 77, 4
+    s0 = _rand_state(R, n, 52)
+    T = [0.6]
+    ref = oracle.run(J, T, sigma, alpha, R, seed=seed, stream=stream, h=h, s0=s0, want_phi=True,
+                     want_state=True)
+    g = Gpu(J, h=h, precision=prec)
+    out = g.run(T, sigma, alpha, R, seed=seed, stream_id=stream, s0=s0, want_phi=True, want_state=True)
+    g.close()
+    scale = phi_scale(J, s0, h, sigma, seed, stream)
+    err = np.abs(out["phi"] - ref["phi"]) / scale
+    assert err.max() <= TOL[prec], (prec, float(err.max()))
+    _check_update(prec, alpha, T[0], s0, out, ref, TOL[prec] * scale)
+
+
 def _check_update(prec, alpha, T, s_prev, out, ref, phi_err):
     """Algorithm 1's Boltzmann update and alpha-mix after one step, element by element:
     (a) the GPU's new state against the update applied in FP64 to the GPU's own Phi
@@ -320,8 +341,9 @@ def test_integer_energies_bit_exact(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_real_valued_energies_fp64(prec):
-    n, R = 120, 16
+@pytest.mark.parametrize("n", [120, 300])  # FP32: the replica-resident and the tiled kernel
+def test_real_valued_energies_fp64(prec, n):
+    R = 16
     J = inst.random_real_couplings(n, 13, density=0.7)
     h = inst.random_fields(n, 0.7, 14)
     g = Gpu(J, h=h, precision=prec)
