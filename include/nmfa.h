@@ -249,8 +249,10 @@ typedef struct nmfa_batch nmfa_batch;
 
 /* Plans the batch (tiles of 128 spins x 64, 128 or 256 replicas; the tile pipelines of
  * one replica block are co-scheduled on the persistent grid by list scheduling),
- * allocates its workspace, uploads the plan and, with NMFA_BATCH_GRAPH, captures the
- * launch sequence as a CUDA graph.  Nothing runs until nmfa_batch_launch.  The
+ * allocates its workspace, uploads the plan, widens FP8-stored problems of n_pad <=
+ * 4096 to BF16 (see NMFA_BATCH_FP8_IN_KERNEL) and, with NMFA_BATCH_GRAPH, captures the
+ * launch sequence as a CUDA graph; it returns once that work has finished on the
+ * batch's own stream.  No run starts until nmfa_batch_launch.  The
  * problems and every device buffer named in `jobs` must stay valid while the batch
  * exists; each launch overwrites the outputs. */
 int nmfa_batch_create(nmfa_problem* const* problems, const nmfa_job* jobs, int32_t count,
